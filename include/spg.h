@@ -1,0 +1,325 @@
+/*
+ * spg.h -- C ABI of the tiled composite SpMV library for power-law graphs
+ * (GB300, sm_103a).
+ *
+ * The method is the one of Yang, Parthasarathy and Sadayappan, "Fast Sparse
+ * Matrix-Vector Multiplication on GPUs: Implications for Graph Mining":
+ * columns (and, symmetrically, rows) reordered by decreasing column length
+ * (Section 3.1, Solution 2), the dense prefix cut into column tiles
+ * (Solution 1, Algorithm 1), every tile stored as a composite of row-major
+ * (CSR-vector) and column-major (ELL) rectangular workloads, one warp each
+ * (Solution 3), with the workload size picked by a performance model
+ * (Section 3.3, Algorithms 2-3), and the power iterations of Appendix F
+ * (PageRank Eq. 6, HITS Eqs. 7-8, Random Walk with Restart Eq. 9) on top.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an spg_status; no exception or longjmp crosses the
+ *    ABI.  SPG_NOT_CONVERGED is a positive warning: outputs are written.
+ *  - Vectors are FP32, in ORIGINAL node order, and may be device pointers or
+ *    host pointers (pageable or pinned); the library detects which with
+ *    cudaPointerGetAttributes and stages host data through its own device
+ *    workspace.  The caller owns every vector; the library keeps no caller
+ *    pointer after a call returns.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls on
+ *    device vectors are asynchronous on that stream; calls that take or
+ *    return host vectors, and calls that report iteration counts, synchronise
+ *    it before returning.  Errors of earlier asynchronous work surface as
+ *    SPG_ERR_CUDA at the next synchronising call.
+ *  - A handle owns its device format and one workspace.  It is
+ *    thread-compatible, not thread-safe: concurrent calls on one handle race;
+ *    use one handle per stream.
+ */
+#ifndef SPG_H
+#define SPG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spg_format_t *spg_handle;
+
+typedef enum {
+    SPG_OK = 0,
+    SPG_NOT_CONVERGED = 1,      /* max_iter reached before tol; outputs written */
+    SPG_ERR_INVALID = -1,       /* bad argument or malformed CSR */
+    SPG_ERR_OOM = -2,           /* host or device allocation failed */
+    SPG_ERR_CUDA = -3,          /* a CUDA call failed (spg_last_error() has text) */
+    SPG_ERR_TIMEOUT = -4,       /* a bounded device-side wait ran out */
+    SPG_ERR_UNSUPPORTED = -5    /* operation not available for this matrix kind */
+} spg_status;
+
+/* What the CSR given to spg_build_format describes. */
+typedef enum {
+    /* The CSR is the square matrix itself (values used).  spmv/spmm only. */
+    SPG_KIND_MATRIX = 0,
+    /* The CSR is the adjacency A of a directed graph (rows = source; values
+     * ignored).  The library builds M = W^T with W the row-normalised A,
+     * M(v,u) = fl32(1/outdeg(u)) for every edge u->v (Appendix F, Eq. 6);
+     * spmv multiplies by M; pagerank and rwr iterate on it. */
+    SPG_KIND_PAGERANK = 1,
+    /* The CSR is A; the library builds the 2n x 2n block matrix
+     * [[0, A^T], [A, 0]] of Eq. 8 with unit values; hits iterates on it and
+     * spmv multiplies by it (vectors of length 2n: authorities then hubs). */
+    SPG_KIND_HITS = 2,
+    /* The CSR is A and `val` holds per-edge logits theta (A's CSR order).
+     * M(v,u) = softmax over u's out-edges of theta; rwr_weighted and
+     * rwr_adjoint use it, and spg_set_edge_logits rewrites it in place. */
+    SPG_KIND_WEIGHTED = 3
+} spg_kind;
+
+/* Compressed sparse rows: n_rows + 1 row offsets (int64), nnz column indices
+ * (int32, each in [0, n_cols)), nnz values (FP32, may be NULL when the kind
+ * ignores values).  Pointers are host memory unless on_device != 0.  The
+ * builder copies what it needs; the arrays may be freed after the call. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const float *val;
+    int on_device;
+} spg_csr;
+
+/* Build options.  Zero-initialise, then set what you need. */
+typedef struct {
+    /* Column tile width (Section 3.1, Solution 1; Algorithm 1).  0 = auto:
+     * the largest power of two whose x slice (tile_width * 4 * vec_width
+     * bytes) fits in 40 % of the L2; < 0 = no dense tiles (the whole matrix is
+     * one composite tile). */
+    int64_t tile_width;
+    /* Workload size per warp (Solution 3).  0 = Algorithm 2. */
+    int64_t wl;
+    /* Rows longer than this are cut into chunks of this many entries, each
+     * its own warp, combined in fixed order (not in the paper; GB300).  -1 =
+     * tuned by the performance model, 0 = never split, > 0 = fixed. */
+    int64_t heavy_row;
+    /* Storage rule of a workload: 0 = the paper's (row-major iff w >= h),
+     * 1 = the major with fewer padded slots (row-major on a tie).  Default 1. */
+    int layout_rule;
+    /* Maximum resident warps of the whole GPU used by Algorithms 2-3.
+     * 0 = query the current device (SMs x resident warps of the kernel). */
+    int max_warps;
+    /* Vector width the tiles are sized for: 1 for spmv, k for spmm. */
+    int vec_width;
+    /* Also build the transposed layout (for spg_rwr_adjoint). */
+    int build_transpose;
+    /* Keep the host copy of the layout plan for spg_format_export_* calls. */
+    int keep_plan;
+    /* Keep the CSR of M in original order on the device for the plain
+     * CSR-scalar / CSR-vector baselines (spg_baseline_*). */
+    int keep_csr;
+    /* -1 = build on the host only (no device upload; for inspecting the
+     * layout on a machine without a GPU); otherwise the current device. */
+    int device;
+    /* Modelled cost, in seconds, of one chunk of a split row (added to the
+     * Algorithm 3 time when tuning heavy_row).  0 = default. */
+    double split_cost;
+    /* Path of a performance table (text, see spg_load_table) or NULL for the
+     * table built into the library. */
+    const char *tune_table_path;
+} spg_build_opts;
+
+/* Per-call results of the power iterations. */
+typedef struct {
+    int iters;          /* iterations run */
+    double last_l1;     /* L1 change of the last iteration (max over columns for k > 1) */
+    double dangling;    /* dangling mass of the final iterate */
+    float ms;           /* device time of the solve (CUDA events) */
+} spg_iter_info;
+
+/* Summary of a built format. */
+typedef struct {
+    int64_t n, nnz;             /* matrix size and non-zeros */
+    int64_t ntile;              /* dense tiles (Algorithm 1); parts = ntile + 1 */
+    int64_t tile_width;
+    int64_t nworkloads;         /* over all parts, zero-row workloads included */
+    int64_t padded_slots;       /* stored slots (non-zeros + padding) */
+    int64_t split_rows, split_chunks;
+    int64_t zero_rows;          /* rows with no entry in any tile */
+    int64_t device_bytes;       /* device memory held by the format */
+    int64_t max_warps;          /* value used by the model */
+    double predicted_ms;        /* Algorithm 3 time summed over parts */
+    int64_t dangling_start;     /* first position of the dangling tail (kind PAGERANK/WEIGHTED) */
+} spg_format_info_t;
+
+/* One part (dense tile or the sparse remainder) of a format. */
+typedef struct {
+    int64_t col_begin, col_end; /* permuted column range */
+    int64_t heavy;              /* split threshold used (0 = none) */
+    int64_t wl;                 /* workload size (Algorithm 2) */
+    int64_t nvirt;              /* ranked (virtual) rows */
+    int64_t nwl;                /* workloads, zero-row workloads excluded */
+    int64_t nnz;                /* non-zeros in the part */
+    double predicted_ms;
+} spg_tile_info_t;
+
+/* ---------------------------------------------------------------- build -- */
+
+/* Build the tiled composite format of the matrix the CSR describes (see
+ * spg_kind), on the host (C++), and upload it to the current device.
+ * Steps: transform (Appendix F), symmetric order by decreasing column length
+ * with ties by ascending id (Solution 2, counting sort as in the "Sorting
+ * Cost" paragraph), Algorithm 1 tiles, per part the in-tile row ranking,
+ * heavy-row split, Algorithm 2 workload size and packing (Solution 3).
+ * `opts` may be NULL (all defaults).  On success *out owns the format.
+ * Errors: SPG_ERR_INVALID for a non-square matrix, row_ptr not starting at 0
+ * or not non-decreasing, row_ptr[n] != nnz, a column out of range, n >= 2^28;
+ * SPG_ERR_OOM; SPG_ERR_CUDA. */
+spg_status spg_build_format(const spg_csr *csr, spg_kind kind, const spg_build_opts *opts,
+                            void *stream, spg_handle *out);
+
+/* Free a handle and everything it owns (device memory included).  NULL is ok. */
+spg_status spg_destroy(spg_handle h);
+
+spg_status spg_format_info(spg_handle h, spg_format_info_t *info);
+spg_status spg_tile_info(spg_handle h, int64_t part, spg_tile_info_t *info);
+
+/* Symmetric permutation: pi[orig] = position, inv[position] = orig (host
+ * arrays of n int32; either may be NULL). */
+spg_status spg_format_perm(spg_handle h, int32_t *pi, int32_t *inv);
+
+/* Plan of one part (needs keep_plan): the ranking of its (virtual) rows --
+ * permuted row id, chunk index, length -- and per workload its first rank,
+ * height h, width w (length of its first row) and major (0 row, 1 column).
+ * Host arrays sized nvirt and nwl from spg_tile_info; any may be NULL. */
+spg_status spg_format_export_plan(spg_handle h, int64_t part, int64_t *rank_row,
+                                  int64_t *rank_chunk, int64_t *rank_len,
+                                  int64_t *wl_first, int64_t *wl_h, int64_t *wl_w,
+                                  int64_t *wl_major);
+
+/* Every stored non-zero as (row, col, value) in ORIGINAL ids, read back from
+ * the packed device (or host-only) layout, padding skipped, split chunks
+ * merged: nnz entries into host arrays, in storage order. */
+spg_status spg_format_export_entries(spg_handle h, int64_t *rows, int32_t *cols, float *vals);
+
+/* Rows (permuted ids) with no entry in any part, ascending (host, zero_rows). */
+spg_status spg_format_zero_rows(spg_handle h, int64_t *rows);
+
+/* ----------------------------------------------------------------- SpMV -- */
+
+/* y = alpha * M x + beta * y (Appendix B's y = A x, on the matrix of the
+ * handle's kind).  x, y: n FP32, original order.  beta == 0: y is not read.
+ * The product runs one tiled-composite launch per part in order (Solution 1:
+ * "we restart a kernel for each tile"), FP32 accumulation, no atomics on y;
+ * x is gathered into the permuted order before and y scattered after. */
+spg_status spg_spmv(spg_handle h, const float *x, float *y, float alpha, float beta,
+                    void *stream);
+
+/* Same product with x and y already in the handle's permuted order (device
+ * pointers only): y' = M' x', no permutation passes. */
+spg_status spg_spmv_permuted(spg_handle h, const float *x_perm, float *y_perm, void *stream);
+
+/* Y = alpha * M X + beta * Y for k vectors: X (n x k) and Y (n x k) FP32,
+ * row-major with leading dimensions ldx, ldy >= k, original row order.
+ * One warp per row, each lane two of the k columns.  k in [1, 1024]. */
+spg_status spg_spmm(spg_handle h, const float *X, int64_t ldx, float *Y, int64_t ldy, int k,
+                    float alpha, float beta, void *stream);
+
+/* ------------------------------------------------------ power iterations -- */
+
+/* PageRank, Appendix F Eq. 6: p <- c M p + (c * sum_{u dangling} p_u + 1 - c)/n,
+ * from p0 (NULL = uniform 1/n), until ||p(k+1) - p(k)||_1 < tol or max_iter
+ * (tol <= 0: exactly max_iter iterations).  The damping, dangling mass, L1
+ * norm and the swap of iterates are fused into the last tile's epilogue; the
+ * scalars are FP64; the loop runs inside one CUDA graph with a conditional
+ * WHILE node (no host round trip per iteration).  p_out: n FP32, original
+ * order.  Kind PAGERANK only.  Returns SPG_NOT_CONVERGED if tol > 0 was not
+ * reached. */
+spg_status spg_pagerank(spg_handle h, float damping, double tol, int max_iter,
+                        const float *p0, float *p_out, spg_iter_info *info, void *stream);
+
+/* Random Walk with Restart, Appendix F Eq. 9 on M (personalised PageRank):
+ * r <- c M r + [v == s] (c * dangling mass + 1 - c), r(0) = e_s, for each of
+ * the k restart nodes seeds[0..k) (host int32, original ids).  k == 1 runs
+ * SpMV iterations; k > 1 runs them as one SpMM over the n x k block (R is
+ * n x k row-major, original order); columns that converge keep iterating
+ * until all have (their L1 stays below tol).  restart = 1 - c.
+ * Kind PAGERANK. */
+spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds, int k, double tol,
+                   int max_iter, float *R, spg_iter_info *info, void *stream);
+
+/* HITS, Appendix F Eqs. 7-8 (Jacobi form) as one SpMV on [[0,A^T],[A,0]]:
+ * a(0) = h(0) = 1/n, each half normalised separately every iteration
+ * (norm = 2: Euclidean, the default; norm = 1: sum, as in the paper).
+ * Exactly max_iter iterations (tol is reserved and must be <= 0).  auth,
+ * hub: n FP32, original order.  Kind HITS. */
+spg_status spg_hits(spg_handle h, int norm, double tol, int max_iter, float *auth, float *hub,
+                    spg_iter_info *info, void *stream);
+
+/* ------------------------------------------------- differentiable RWR -- */
+
+/* Rewrite the transition weights of a WEIGHTED handle from per-edge logits
+ * theta (nnz FP32, A's CSR order, device or host): P_e = softmax over the
+ * out-edges of each node, written straight into the packed slots of the
+ * forward (and transposed) layout through the stored edge map. */
+spg_status spg_set_edge_logits(spg_handle h, const float *theta, void *stream);
+
+/* RWR fixed point on a WEIGHTED handle: r = c K r + (1-c) e_s with
+ * K = M + e_s 1_D^T (dangling mass returns to s); r: n FP32, original order. */
+spg_status spg_rwr_weighted(spg_handle h, float restart, int32_t seed, double tol, int max_iter,
+                            float *r, spg_iter_info *info, void *stream);
+
+/* Adjoint of spg_rwr_weighted (not in the paper): given r and g = dL/dr
+ * (n FP32 each, original order), solve lambda = c K^T lambda + g by
+ * transposed-SpMV iterations on the stored transposed layout (needs
+ * build_transpose), then dL/dtheta_e = P_e (G_e - sum_{e' in out(u)} P_e' G_e')
+ * with G_e = c lambda_v r_u for e = u -> v.  lambda: n FP32; dtheta: nnz FP32
+ * in A's CSR order.  No iterate checkpointing: the fixed point is
+ * differentiated implicitly. */
+spg_status spg_rwr_adjoint(spg_handle h, float restart, int32_t seed, const float *r,
+                           const float *g, double tol, int max_iter, float *lambda,
+                           float *dtheta, spg_iter_info *info, void *stream);
+
+/* ------------------------------------------------------ batched graphs -- */
+
+/* PageRank on `count` independent PAGERANK handles at once, in ONE persistent
+ * launch per iteration sweep, the whole solve captured in a CUDA graph (not
+ * in the paper; batching of small graphs).  Graphs are scheduled longest
+ * first over the SMs; each graph runs its own tolerance test.  p_out[g] is
+ * graph g's n_g FP32 output (device pointers); info (nullable) gets one
+ * entry per graph. */
+spg_status spg_batch_pagerank(const spg_handle *graphs, int count, float damping, double tol,
+                              int max_iter, float *const *p_out, spg_iter_info *info,
+                              void *stream);
+
+/* ------------------------------------------------------------ baselines -- */
+
+typedef enum { SPG_BASELINE_CSR_SCALAR = 0, SPG_BASELINE_CSR_VECTOR = 1 } spg_baseline;
+
+/* The plain CSR kernels of Appendix B on the CSR of M in original order
+ * (needs keep_csr): CSR-scalar (one thread per row) and CSR-vector (one warp
+ * per row).  Same semantics as spg_spmv / spg_pagerank. */
+spg_status spg_baseline_spmv(spg_handle h, spg_baseline which, const float *x, float *y,
+                             float alpha, float beta, void *stream);
+spg_status spg_baseline_pagerank(spg_handle h, spg_baseline which, float damping, double tol,
+                                 int max_iter, float *p_out, spg_iter_info *info, void *stream);
+
+/* -------------------------------------------------------------- misc -- */
+
+/* Load a performance table (Section 3.3 lookup table) for the process: text
+ * lines "major log2w log2h perf" (perf in slots/s); missing shapes take the
+ * nearest measured bucket.  NULL restores the built-in table. */
+spg_status spg_load_table(const char *path);
+
+/* Measurement: time each part's tiled-composite kernel alone, `reps`
+ * back-to-back launches per part between two CUDA events on `stream`, and
+ * write the mean launch duration (ms) of part p to ms_out[p] (host array of
+ * ntile + 1 floats).  mode 0: the plain SpMV kernel (x' and y' are the
+ * handle's workspace, contents arbitrary); mode 1: the PageRank epilogue
+ * kernel on the state of the last spg_pagerank call on this handle. */
+spg_status spg_time_parts(spg_handle h, int mode, int reps, float *ms_out, void *stream);
+
+/* Kernel launches this library issued since load (all entry points). */
+int64_t spg_launch_count(void);
+
+const char *spg_status_string(spg_status s);
+/* Text of the last error on the calling thread ("" if none). */
+const char *spg_last_error(void);
+/* Library version string. */
+const char *spg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPG_H */

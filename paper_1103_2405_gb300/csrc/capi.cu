@@ -1,0 +1,1037 @@
+// capi.cu -- the extern "C" boundary (include/spg.h): handles, workspace,
+// the power-iteration drivers and the exports of the layout plan.
+//
+// Power iterations run entirely on the device: per iteration one launch per
+// part with the fused epilogue (Appendix F) and one check kernel that sums
+// the per-block FP64 partials in a fixed order, updates the scalars and the
+// ping-pong parity, and sets the conditional of a CUDA-graph WHILE node, so
+// the loop needs no host round trip.  Graphs are built once per handle and
+// loop kind and reused (every parameter lives in device memory).
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/spg.h"
+#include "format.h"
+#include "kernels.h"
+
+using namespace spg;
+
+static thread_local std::string g_err;
+
+static spg_status fail(spg_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+static spg_status cuda_fail(cudaError_t e, const char *where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return SPG_ERR_CUDA;
+}
+
+#define CK(call)                                                       \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);            \
+    } while (0)
+
+namespace {
+
+struct LoopGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kernels_per_iter = 0;
+};
+
+// Device buffer that grows on demand.  A reallocation bumps *epoch, which
+// invalidates every cached loop graph (they capture buffer addresses).
+template <class T> struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    uint64_t *epoch = nullptr;
+    cudaError_t ensure(size_t count)
+    {
+        if (count <= n && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        if (epoch) ++*epoch;
+        cudaError_t e = cudaMalloc((void **)&p, std::max<size_t>(1, count) * sizeof(T));
+        if (e == cudaSuccess) n = count;
+        return e;
+    }
+    void release() { if (p) cudaFree(p); p = nullptr; n = 0; }
+};
+
+}  // namespace
+
+struct spg_format_t {
+    spg_kind kind = SPG_KIND_MATRIX;
+    int device = 0;
+    bool host_only = false;
+    int64_t n_graph = 0;       // nodes of the graph (HITS: layout is 2n)
+    int64_t nnz_in = 0;        // non-zeros of the input CSR
+    Layout fwd;
+    std::unique_ptr<Layout> bwd;
+    // baselines: M in original order
+    int64_t *d_rp = nullptr;
+    int32_t *d_col = nullptr;
+    float *d_val = nullptr;
+    uint8_t *d_dangling = nullptr;
+    // HITS: per permuted position, 1 if in the hub half
+    uint8_t *d_row_half = nullptr;
+    // WEIGHTED: A on the device and the current transition weights
+    int64_t *d_arp = nullptr;
+    int32_t *d_acol = nullptr;
+    float *d_P = nullptr;
+    // workspace
+    DevBuf<float> x, y, stage_in, stage_out;
+    DevBuf<double2> red;
+    DevBuf<double> redk, delta_k, l1_k;
+    DevBuf<float> partial_k;
+    DevBuf<int32_t> seeds;
+    DevBuf<float> X, Y;
+    IterState *d_state = nullptr;
+    std::map<std::string, LoopGraph> graphs;
+    uint64_t epoch = 0;          // workspace generation the cached graphs were built for
+    uint64_t graphs_epoch = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    spg_format_t()
+    {
+        for (DevBuf<float> *b : {&x, &y, &partial_k, &X, &Y}) b->epoch = &epoch;
+        red.epoch = &epoch;
+        redk.epoch = &epoch;
+        delta_k.epoch = &epoch;
+        l1_k.epoch = &epoch;
+        seeds.epoch = &epoch;
+    }
+
+    void drop_graphs()
+    {
+        for (auto &kv : graphs) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+        }
+        graphs.clear();
+    }
+
+    ~spg_format_t()
+    {
+        if (host_only) return;
+        fwd.free_device();
+        if (bwd) bwd->free_device();
+        cudaFree(d_rp); cudaFree(d_col); cudaFree(d_val); cudaFree(d_dangling);
+        cudaFree(d_row_half); cudaFree(d_arp); cudaFree(d_acol); cudaFree(d_P);
+        x.release(); y.release(); stage_in.release(); stage_out.release(); red.release();
+        redk.release(); delta_k.release(); l1_k.release(); partial_k.release(); seeds.release();
+        X.release(); Y.release();
+        cudaFree(d_state);
+        for (auto &kv : graphs) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+        }
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+};
+
+// ------------------------------------------------------------------ util --
+
+static bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int64_t pow2_floor(int64_t v)
+{
+    int64_t p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+// Resolved tile width: explicit, none (< 0), or auto from the L2 size.
+static int64_t resolve_tile_width(const spg_build_opts &o, int64_t l2_bytes)
+{
+    if (o.tile_width > 0) return o.tile_width;
+    if (o.tile_width < 0) return 0;
+    int vw = o.vec_width > 0 ? o.vec_width : 1;
+    int64_t cols = (int64_t)(0.4 * (double)l2_bytes) / (4 * (int64_t)vw);
+    return pow2_floor(std::max<int64_t>(cols, 1024));
+}
+
+static spg_status check_csr(const spg_csr *c, std::vector<int64_t> &rp, std::vector<int32_t> &col,
+                            std::vector<float> &val, const int64_t *&prp, const int32_t *&pcol,
+                            const float *&pval)
+{
+    if (!c || c->n_rows < 1 || c->n_rows != c->n_cols || c->nnz < 0)
+        return fail(SPG_ERR_INVALID, "CSR must be square with n >= 1 and nnz >= 0");
+    if (c->n_rows >= kMaxN) return fail(SPG_ERR_INVALID, "n must be < 2^28");
+    if (!c->row_ptr || (c->nnz > 0 && !c->col)) return fail(SPG_ERR_INVALID, "null CSR array");
+    const int64_t n = c->n_rows, nnz = c->nnz;
+    prp = c->row_ptr; pcol = c->col; pval = c->val;
+    if (c->on_device) {
+        rp.resize((size_t)n + 1);
+        CK(cudaMemcpy(rp.data(), c->row_ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        col.resize((size_t)nnz);
+        if (nnz) CK(cudaMemcpy(col.data(), c->col, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (c->val) {
+            val.resize((size_t)nnz);
+            if (nnz) CK(cudaMemcpy(val.data(), c->val, nnz * sizeof(float), cudaMemcpyDeviceToHost));
+            pval = val.data();
+        }
+        prp = rp.data(); pcol = col.data();
+    }
+    if (prp[0] != 0 || prp[n] != nnz) return fail(SPG_ERR_INVALID, "row_ptr[0] != 0 or row_ptr[n] != nnz");
+    std::atomic<bool> bad{false};
+    parallel_for(n, 1 << 16, [&](int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi && !bad; ++i)
+            if (prp[i + 1] < prp[i]) bad = true;
+    });
+    if (bad) return fail(SPG_ERR_INVALID, "row_ptr is not non-decreasing");
+    parallel_for(nnz, 1 << 18, [&](int64_t lo, int64_t hi) {
+        for (int64_t k = lo; k < hi && !bad; ++k)
+            if (pcol[k] < 0 || pcol[k] >= n) bad = true;
+    });
+    if (bad) return fail(SPG_ERR_INVALID, "column index out of range");
+    return SPG_OK;
+}
+
+// CSR (by rows) -> CSC of the same matrix: colptr, rowidx, val, entry ids.
+static void csr_to_csc(int64_t n, const int64_t *rp, const int32_t *col, const float *val,
+                       std::vector<int64_t> &cp, std::vector<int32_t> &ri, std::vector<float> &cv,
+                       std::vector<int64_t> &eid)
+{
+    const int64_t nnz = rp[n];
+    cp.assign((size_t)n + 1, 0);
+    for (int64_t k = 0; k < nnz; ++k) cp[(size_t)col[k] + 1]++;
+    for (int64_t j = 0; j < n; ++j) cp[(size_t)j + 1] += cp[(size_t)j];
+    std::vector<int64_t> fill(cp.begin(), cp.end() - 1);
+    ri.resize((size_t)nnz); cv.resize((size_t)nnz); eid.resize((size_t)nnz);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            int64_t s = fill[(size_t)col[k]]++;
+            ri[(size_t)s] = (int32_t)i;
+            cv[(size_t)s] = val ? val[k] : 1.0f;
+            eid[(size_t)s] = k;
+        }
+}
+
+template <class T> static cudaError_t upload(T **d, const T *h, size_t count)
+{
+    cudaError_t e = cudaMalloc((void **)d, std::max<size_t>(1, count) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (count) e = cudaMemcpy(*d, h, count * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+static int64_t query_max_warps()
+{
+    int dev = 0, sms = 0, blocks = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 9728;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    blocks = part_blocks_per_sm();
+    if (blocks <= 0) {
+        int per = 0;
+        cudaDeviceGetAttribute(&per, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+        blocks = per / kBlock;
+    }
+    return (int64_t)sms * blocks * kWarpsPerBlock;
+}
+
+// ----------------------------------------------------------------- build --
+
+extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
+                                       const spg_build_opts *opts_in, void *stream,
+                                       spg_handle *out)
+{
+    try {
+        if (!out) return fail(SPG_ERR_INVALID, "out is NULL");
+        *out = nullptr;
+        spg_build_opts o;
+        std::memset(&o, 0, sizeof o);
+        o.heavy_row = -1;
+        o.layout_rule = 1;
+        if (opts_in) o = *opts_in;
+        if (kind < SPG_KIND_MATRIX || kind > SPG_KIND_WEIGHTED) return fail(SPG_ERR_INVALID, "bad kind");
+        std::vector<int64_t> hrp;
+        std::vector<int32_t> hcol;
+        std::vector<float> hval;
+        const int64_t *rp;
+        const int32_t *col;
+        const float *val;
+        spg_status st = check_csr(csr, hrp, hcol, hval, rp, col, val);
+        if (st != SPG_OK) return st;
+        if (kind == SPG_KIND_MATRIX && !val) return fail(SPG_ERR_INVALID, "MATRIX kind needs values");
+        if (kind == SPG_KIND_WEIGHTED && !val) return fail(SPG_ERR_INVALID, "WEIGHTED kind needs logits");
+        const int64_t n = csr->n_rows, nnz = csr->nnz;
+        if (kind == SPG_KIND_HITS && 2 * n >= kMaxN) return fail(SPG_ERR_INVALID, "2n must be < 2^28");
+
+        std::unique_ptr<spg_format_t> h(new spg_format_t());
+        h->kind = kind;
+        h->host_only = o.device < 0;
+        h->n_graph = n;
+        h->nnz_in = nnz;
+        cudaStream_t s = (cudaStream_t)stream;
+        int64_t l2 = 126LL << 20;
+        if (!h->host_only) {
+            CK(cudaGetDevice(&h->device));
+            int l2i = 0;
+            cudaDeviceGetAttribute(&l2i, cudaDevAttrL2CacheSize, h->device);
+            if (l2i > 0) l2 = l2i;
+        }
+        BuildParams prm;
+        prm.tile_width = resolve_tile_width(o, l2);
+        prm.wl = o.wl;
+        prm.heavy = o.heavy_row;
+        prm.layout_rule = o.layout_rule == 0 ? 0 : 1;
+        prm.max_warps = o.max_warps > 0 ? o.max_warps : (h->host_only ? 9728 : query_max_warps());
+        if (o.split_cost > 0) prm.split_cost = o.split_cost;
+        prm.keep_plan = o.keep_plan != 0;
+        prm.track_edges = kind == SPG_KIND_WEIGHTED;
+        if (o.tune_table_path) {
+            std::string err;
+            if (!perf_table_load(o.tune_table_path, perf_table(), err)) return fail(SPG_ERR_INVALID, err);
+        }
+
+        // column source of the matrix to format
+        ColumnSource src;
+        std::vector<int64_t> cp, eid;
+        std::vector<int32_t> ri;
+        std::vector<float> cv;
+        std::vector<uint8_t> rclass;
+        std::vector<float> mval;   // PAGERANK values per entry of A
+        if (kind == SPG_KIND_MATRIX) {
+            csr_to_csc(n, rp, col, val, cp, ri, cv, eid);
+            src.n = n; src.colptr = cp.data(); src.rowidx = ri.data(); src.val = cv.data();
+            src.eid = eid.data();
+        } else if (kind == SPG_KIND_PAGERANK || kind == SPG_KIND_WEIGHTED) {
+            // column u of M = row u of A; value fl32(1/outdeg(u)) (Eq. 6), or the
+            // softmax of u's logits (WEIGHTED)
+            mval.resize((size_t)nnz);
+            parallel_for(n, 1 << 14, [&](int64_t lo, int64_t hi) {
+                for (int64_t u = lo; u < hi; ++u) {
+                    const int64_t b = rp[u], e = rp[u + 1];
+                    if (b == e) continue;
+                    if (kind == SPG_KIND_PAGERANK) {
+                        const float w = (float)(1.0 / (double)(e - b));
+                        for (int64_t k = b; k < e; ++k) mval[(size_t)k] = w;
+                    } else {
+                        double m = -INFINITY, sum = 0.0;
+                        for (int64_t k = b; k < e; ++k) m = std::max(m, (double)val[k]);
+                        for (int64_t k = b; k < e; ++k) sum += std::exp((double)val[k] - m);
+                        for (int64_t k = b; k < e; ++k)
+                            mval[(size_t)k] = (float)(std::exp((double)val[k] - m) / sum);
+                    }
+                }
+            });
+            src.n = n; src.colptr = rp; src.rowidx = col; src.val = mval.data(); src.eid = nullptr;
+        } else {  // HITS: B = [[0, A^T], [A, 0]] of Eq. 8
+            // column v < n: rows n+u for edges u->v (A's CSC); column n+u: rows v (A's CSR row u)
+            std::vector<int64_t> acp, aeid;
+            std::vector<int32_t> ari;
+            std::vector<float> acv;
+            csr_to_csc(n, rp, col, nullptr, acp, ari, acv, aeid);
+            cp.assign((size_t)(2 * n + 1), 0);
+            for (int64_t j = 0; j < n; ++j) cp[(size_t)j + 1] = cp[(size_t)j] + (acp[(size_t)j + 1] - acp[(size_t)j]);
+            for (int64_t u = 0; u < n; ++u) cp[(size_t)(n + u + 1)] = cp[(size_t)(n + u)] + (rp[u + 1] - rp[u]);
+            ri.resize((size_t)(2 * nnz));
+            cv.assign((size_t)(2 * nnz), 1.0f);
+            for (int64_t j = 0; j < n; ++j)
+                for (int64_t k = acp[(size_t)j], q = cp[(size_t)j]; k < acp[(size_t)j + 1]; ++k, ++q)
+                    ri[(size_t)q] = (int32_t)(n + ari[(size_t)k]);
+            for (int64_t u = 0; u < n; ++u)
+                for (int64_t k = rp[u], q = cp[(size_t)(n + u)]; k < rp[u + 1]; ++k, ++q)
+                    ri[(size_t)q] = col[k];
+            rclass.assign((size_t)(2 * n), 0);
+            for (int64_t i = n; i < 2 * n; ++i) rclass[(size_t)i] = 1;
+            src.n = 2 * n; src.colptr = cp.data(); src.rowidx = ri.data(); src.val = cv.data();
+            src.row_class = rclass.data();
+        }
+        std::string err;
+        if (!build_layout(src, prm, h->fwd, err)) return fail(SPG_ERR_INVALID, err);
+
+        if (!h->host_only) {
+            cudaError_t e = upload_layout(h->fwd, o.keep_plan != 0, s);
+            if (e == cudaErrorMemoryAllocation) return fail(SPG_ERR_OOM, "device memory for the format");
+            if (e != cudaSuccess) return cuda_fail(e, "upload");
+            const int64_t N = h->fwd.n;
+            CK(cudaMalloc((void **)&h->d_state, sizeof(IterState)));
+            CK(cudaEventCreate(&h->ev0));
+            CK(cudaEventCreate(&h->ev1));
+            if (kind == SPG_KIND_HITS) {
+                std::vector<uint8_t> half((size_t)N);
+                for (int64_t k = 0; k < N; ++k) half[(size_t)k] = h->fwd.inv[(size_t)k] >= n ? 1 : 0;
+                CK(upload(&h->d_row_half, half.data(), half.size()));
+            }
+            if (o.keep_csr && (kind == SPG_KIND_PAGERANK || kind == SPG_KIND_MATRIX)) {
+                // M in original order by rows: transpose of the column source
+                std::vector<int64_t> mrp, meid;
+                std::vector<int32_t> mcol;
+                std::vector<float> mv;
+                csr_to_csc(n, src.colptr, src.rowidx, src.val, mrp, mcol, mv, meid);
+                CK(upload(&h->d_rp, mrp.data(), mrp.size()));
+                CK(upload(&h->d_col, mcol.data(), mcol.size()));
+                CK(upload(&h->d_val, mv.data(), mv.size()));
+                std::vector<uint8_t> dang((size_t)n);
+                for (int64_t u = 0; u < n; ++u) dang[(size_t)u] = (src.colptr[u + 1] == src.colptr[u]) ? 1 : 0;
+                CK(upload(&h->d_dangling, dang.data(), dang.size()));
+            }
+            if (kind == SPG_KIND_WEIGHTED) {
+                CK(upload(&h->d_arp, rp, (size_t)n + 1));
+                CK(upload(&h->d_acol, col, (size_t)nnz));
+                CK(upload(&h->d_P, mval.data(), (size_t)nnz));
+                if (o.build_transpose) {
+                    // M^T: rows u (sources), entries (v, P_e) -> column source of M^T is
+                    // M's CSR by rows, i.e. the CSC of A's pattern with values P
+                    std::vector<int64_t> tcp, teid;
+                    std::vector<int32_t> tri;
+                    std::vector<float> tcv;
+                    csr_to_csc(n, rp, col, mval.data(), tcp, tri, tcv, teid);
+                    ColumnSource ts;
+                    ts.n = n; ts.colptr = tcp.data(); ts.rowidx = tri.data(); ts.val = tcv.data();
+                    ts.eid = teid.data();
+                    h->bwd.reset(new Layout());
+                    if (!build_layout(ts, prm, *h->bwd, err)) return fail(SPG_ERR_INVALID, err);
+                    e = upload_layout(*h->bwd, o.keep_plan != 0, s);
+                    if (e != cudaSuccess) return cuda_fail(e, "upload transpose");
+                }
+            }
+        }
+        *out = h.release();
+        return SPG_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(SPG_ERR_OOM, "host memory");
+    } catch (const std::exception &ex) {
+        return fail(SPG_ERR_INVALID, ex.what());
+    }
+}
+
+extern "C" spg_status spg_destroy(spg_handle h)
+{
+    delete h;
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_format_info(spg_handle h, spg_format_info_t *info)
+{
+    if (!h || !info) return fail(SPG_ERR_INVALID, "null argument");
+    const Layout &L = h->fwd;
+    std::memset(info, 0, sizeof *info);
+    info->n = L.n;
+    info->nnz = L.nnz;
+    info->ntile = L.ntile;
+    info->tile_width = L.tile_width;
+    int64_t nw = 0;
+    double pm = 0;
+    for (const PartHost &p : L.parts) { nw += p.nwl_total; pm += p.predicted_s; }
+    info->nworkloads = nw;
+    info->padded_slots = L.padded_slots;
+    info->split_rows = L.nsplit;
+    info->split_chunks = L.nchunk_slots;
+    info->zero_rows = (int64_t)L.zero_rows.size();
+    info->device_bytes = L.device_bytes + (h->bwd ? h->bwd->device_bytes : 0);
+    info->max_warps = L.max_warps;
+    info->predicted_ms = pm * 1e3;
+    info->dangling_start = L.dangling_start;
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_tile_info(spg_handle h, int64_t part, spg_tile_info_t *info)
+{
+    if (!h || !info || part < 0 || part >= (int64_t)h->fwd.parts.size())
+        return fail(SPG_ERR_INVALID, "bad part");
+    const PartHost &p = h->fwd.parts[(size_t)part];
+    info->col_begin = p.c0;
+    info->col_end = p.c1;
+    info->heavy = p.heavy;
+    info->wl = p.wl;
+    info->nvirt = p.nvirt;
+    info->nwl = p.nwl;
+    info->nnz = p.nnz;
+    info->predicted_ms = p.predicted_s * 1e3;
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_format_perm(spg_handle h, int32_t *pi, int32_t *inv)
+{
+    if (!h) return fail(SPG_ERR_INVALID, "null handle");
+    if (pi) std::memcpy(pi, h->fwd.perm.data(), h->fwd.perm.size() * sizeof(int32_t));
+    if (inv) std::memcpy(inv, h->fwd.inv.data(), h->fwd.inv.size() * sizeof(int32_t));
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_format_export_plan(spg_handle h, int64_t part, int64_t *rank_row,
+                                             int64_t *rank_chunk, int64_t *rank_len,
+                                             int64_t *wl_first, int64_t *wl_h, int64_t *wl_w,
+                                             int64_t *wl_major)
+{
+    if (!h || part < 0 || part >= (int64_t)h->fwd.parts.size()) return fail(SPG_ERR_INVALID, "bad part");
+    const PartHost &p = h->fwd.parts[(size_t)part];
+    if ((int64_t)p.rank_len.size() != p.nvirt) return fail(SPG_ERR_INVALID, "plan not kept (keep_plan)");
+    for (int64_t i = 0; i < p.nvirt; ++i) {
+        if (rank_row) rank_row[i] = p.rank_row[(size_t)i];
+        if (rank_chunk) rank_chunk[i] = p.rank_chunk[(size_t)i];
+        if (rank_len) rank_len[i] = p.rank_len[(size_t)i];
+    }
+    for (int64_t j = 0; j < p.nwl; ++j) {
+        if (wl_first) wl_first[j] = p.wl_first[(size_t)j];
+        if (wl_h) wl_h[j] = p.wl_h[(size_t)j];
+        if (wl_w) wl_w[j] = p.wl_w[(size_t)j];
+        if (wl_major) wl_major[j] = p.wl_major[(size_t)j];
+    }
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_format_zero_rows(spg_handle h, int64_t *rows)
+{
+    if (!h || !rows) return fail(SPG_ERR_INVALID, "null argument");
+    std::memcpy(rows, h->fwd.zero_rows.data(), h->fwd.zero_rows.size() * sizeof(int64_t));
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, int32_t *ocols,
+                                                float *ovals)
+{
+    if (!h) return fail(SPG_ERR_INVALID, "null handle");
+    const Layout &L = h->fwd;
+    std::vector<Workload> wl = L.wl;
+    std::vector<uint32_t> rows = L.rows;
+    std::vector<uint2> slab = L.slab;
+    if (wl.empty() && L.on_device) {
+        int64_t nwl = 0;
+        for (const PartHost &p : L.parts) nwl += p.nwl_total;
+        int64_t nrows = 0;
+        for (const PartHost &p : L.parts) nrows += p.nvirt;
+        nrows += (int64_t)L.zero_rows.size();
+        wl.resize((size_t)nwl);
+        rows.resize((size_t)nrows);
+        slab.resize((size_t)L.padded_slots);
+        CK(cudaMemcpy(wl.data(), L.d_wl, nwl * sizeof(Workload), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(rows.data(), L.d_rows, nrows * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        if (L.padded_slots)
+            CK(cudaMemcpy(slab.data(), L.d_slab, L.padded_slots * sizeof(uint2), cudaMemcpyDeviceToHost));
+    }
+    int64_t k = 0;
+    for (const Workload &d : wl) {
+        const int64_t hp = d.major == 0 ? d.h : (d.h + 31) / 32 * 32;
+        for (int64_t i = 0; i < d.h; ++i) {
+            uint32_t rid = rows[(size_t)d.rows + i];
+            uint32_t r = (rid & kRowSplit) ? (L.split[(size_t)L.slot_owner[rid & 0x7fffffffu]].row & kRowIdMask)
+                                           : (rid & kRowIdMask);
+            for (int64_t e = 0; e < d.w; ++e) {
+                int64_t slot = d.major == 0 ? d.slab + i * d.w + e
+                                            : d.slab + (i / 32) * 32 * d.w + e * 32 + (i % 32);
+                uint2 v = slab[(size_t)slot];
+                if ((int32_t)v.x < 0) continue;
+                if (k >= L.nnz) return fail(SPG_ERR_INVALID, "more stored entries than nnz");
+                if (orows) orows[k] = L.inv[r];
+                if (ocols) ocols[k] = L.inv[v.x];
+                if (ovals) std::memcpy(&ovals[k], &v.y, 4);
+                ++k;
+            }
+        }
+        (void)hp;
+    }
+    if (k != L.nnz) return fail(SPG_ERR_INVALID, "stored entries != nnz");
+    return SPG_OK;
+}
+
+// ---------------------------------------------------------------- drivers --
+
+static std::vector<PartView> views_of(const Layout &L) { return L.part_views(); }
+
+static spg_status ensure_vectors(spg_handle h, int64_t N)
+{
+    CK(h->x.ensure((size_t)N));
+    CK(h->y.ensure((size_t)N));
+    CK(h->red.ensure((size_t)std::max<int64_t>(1, h->fwd.nred)));
+    return SPG_OK;
+}
+
+// Input vector on the device: the caller's pointer or a staged copy.
+static spg_status device_in(spg_handle h, const float *p, int64_t count, const float **out,
+                            cudaStream_t s)
+{
+    if (!p || is_device_ptr(p)) { *out = p; return SPG_OK; }
+    CK(h->stage_in.ensure((size_t)count));
+    CK(cudaMemcpyAsync(h->stage_in.p, p, count * sizeof(float), cudaMemcpyHostToDevice, s));
+    *out = h->stage_in.p;
+    return SPG_OK;
+}
+
+static void launch_parts(spg_handle h, int mode, const float *x, float *y, const IterState *st,
+                         double2 *red, cudaStream_t s)
+{
+    const SplitView sv = h->fwd.split_view();
+    for (const PartView &pv : views_of(h->fwd)) launch_part(mode, pv, sv, x, y, st, red, s);
+}
+
+extern "C" spg_status spg_spmv_permuted(spg_handle h, const float *xp, float *yp, void *stream)
+{
+    if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
+    if (!xp || !yp || xp == yp) return fail(SPG_ERR_INVALID, "x and y must be distinct device vectors");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_parts(h, EPI_RAW, xp, yp, nullptr, nullptr, s);
+    CK(cudaGetLastError());
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_spmv(spg_handle h, const float *x, float *y, float alpha, float beta,
+                               void *stream)
+{
+    if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
+    if (!x || !y) return fail(SPG_ERR_INVALID, "null vector");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->fwd.n;
+    spg_status st = ensure_vectors(h, N);
+    if (st != SPG_OK) return st;
+    const float *xd;
+    if ((st = device_in(h, x, N, &xd, s)) != SPG_OK) return st;
+    const bool y_host = !is_device_ptr(y);
+    float *yd = y;
+    if (y_host) {
+        CK(h->stage_out.ensure((size_t)N));
+        yd = h->stage_out.p;
+        if (beta != 0.f) CK(cudaMemcpyAsync(yd, y, N * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    launch_gather(N, h->fwd.d_inv, xd, h->x.p, s);
+    launch_parts(h, EPI_RAW, h->x.p, h->y.p, nullptr, nullptr, s);
+    launch_scatter_axpby(N, h->fwd.d_inv, h->y.p, yd, alpha, beta, s);
+    CK(cudaGetLastError());
+    if (y_host) {
+        CK(cudaMemcpyAsync(y, yd, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_spmm(spg_handle h, const float *X, int64_t ldx, float *Y, int64_t ldy,
+                               int k, float alpha, float beta, void *stream)
+{
+    if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
+    if (!X || !Y || k < 1 || k > 1024 || ldx < k || ldy < k) return fail(SPG_ERR_INVALID, "bad SpMM arguments");
+    if (!is_device_ptr(X) || !is_device_ptr(Y)) return fail(SPG_ERR_INVALID, "spmm takes device pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Layout &L = h->fwd;
+    const int64_t N = L.n;
+    CK(h->X.ensure((size_t)(N * k)));
+    CK(h->Y.ensure((size_t)(N * k)));
+    CK(h->partial_k.ensure((size_t)std::max<int64_t>(1, L.nchunk_slots) * k));
+    launch_gather_rows(N, k, L.d_inv, X, ldx, h->X.p, s);
+    SplitView sv = L.split_view();
+    sv.partial = h->partial_k.p;
+    for (const PartView &pv : views_of(L))
+        launch_part_spmm(EPI_RAW, pv, sv, h->X.p, h->Y.p, k, nullptr, nullptr, nullptr, nullptr, s);
+    launch_scatter_rows(N, k, L.d_inv, h->Y.p, Y, ldy, alpha, beta, s);
+    CK(cudaGetLastError());
+    return SPG_OK;
+}
+
+// Build (once) a graph whose body is `body(stream, cond)` inside a WHILE
+// node; the body's check kernel clears the condition when done.
+template <class Body>
+static spg_status get_loop_graph(spg_handle h, const std::string &key, Body body, LoopGraph **out)
+{
+    if (h->graphs_epoch != h->epoch) {   // a workspace buffer moved: recapture
+        h->drop_graphs();
+        h->graphs_epoch = h->epoch;
+    }
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) { *out = &it->second; return SPG_OK; }
+    LoopGraph g;
+    CK(cudaGraphCreate(&g.graph, 0));
+    cudaGraphConditionalHandle ch;
+    CK(cudaGraphConditionalHandleCreate(&ch, g.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = ch;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const int64_t before = launch_count();
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        body(cs, (unsigned long long)ch);
+        cudaGraph_t captured = bodyg;
+        e = cudaStreamEndCapture(cs, &captured);
+    }
+    g.kernels_per_iter = (int)(launch_count() - before);
+    count_launches(-(launch_count() - before));
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) { cudaGraphDestroy(g.graph); return cuda_fail(e, "capture loop body"); }
+    e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g.graph); return cuda_fail(e, "instantiate loop graph"); }
+    auto res = h->graphs.emplace(key, g);
+    *out = &res.first->second;
+    return SPG_OK;
+}
+
+static IterState make_state(spg_handle h, double c, double tol, int max_iter, int64_t N,
+                            float *b0, float *b1)
+{
+    IterState st;
+    std::memset(&st, 0, sizeof st);
+    st.c = c;
+    st.tol = tol;
+    st.delta = 0.0;
+    st.l1 = INFINITY;
+    st.scale[0] = st.scale[1] = 1.0;
+    st.inv_n = 1.0 / (double)N;
+    st.iter = 0;
+    st.max_iter = max_iter;
+    st.parity = 0;
+    st.done = 0;
+    st.seed = -1;
+    st.hits_norm = 2;
+    st.n = N;
+    st.dangling_start = h->fwd.dangling_start;
+    st.buf[0] = b0;
+    st.buf[1] = b1;
+    return st;
+}
+
+// Run the loop graph `g` (max_iter > 0) and read back the state.
+static spg_status run_loop(spg_handle h, LoopGraph *g, int max_iter, IterState *hs,
+                           spg_iter_info *info, cudaStream_t s)
+{
+    if (max_iter > 0) {
+        CK(cudaEventRecord(h->ev0, s));
+        CK(cudaGraphLaunch(g->exec, s));
+        CK(cudaEventRecord(h->ev1, s));
+    }
+    CK(cudaMemcpyAsync(hs, h->d_state, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    count_launches((int64_t)hs->iter * g->kernels_per_iter);
+    if (info) {
+        info->iters = hs->iter;
+        info->last_l1 = hs->l1;
+        info->dangling = hs->delta;
+        float ms = 0.f;
+        if (max_iter > 0) cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+        info->ms = ms;
+    }
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int max_iter,
+                                   const float *p0, float *p_out, spg_iter_info *info,
+                                   void *stream)
+{
+    if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
+    if (h->kind != SPG_KIND_PAGERANK) return fail(SPG_ERR_UNSUPPORTED, "pagerank needs a PAGERANK handle");
+    if (!p_out || !(damping >= 0.f && damping < 1.f) || max_iter < 0)
+        return fail(SPG_ERR_INVALID, "bad pagerank arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->fwd.n;
+    spg_status st = ensure_vectors(h, N);
+    if (st != SPG_OK) return st;
+    IterState hs = make_state(h, damping, tol, max_iter, N, h->x.p, h->y.p);
+    CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
+    if (p0) {
+        const float *pd;
+        if ((st = device_in(h, p0, N, &pd, s)) != SPG_OK) return st;
+        launch_gather(N, h->fwd.d_inv, pd, h->x.p, s);
+    } else {
+        launch_fill(N, (float)(1.0 / (double)N), h->x.p, s);
+    }
+    launch_init_delta(h->d_state, s);
+    LoopGraph *g;
+    const int nred = (int)h->fwd.nred;
+    st = get_loop_graph(h, "pagerank", [&](cudaStream_t cs, unsigned long long cond) {
+        launch_parts(h, EPI_PAGERANK, nullptr, nullptr, h->d_state, h->red.p, cs);
+        launch_check(EPI_PAGERANK, h->d_state, h->red.p, nred, cond, 1, cs);
+    }, &g);
+    if (st != SPG_OK) return st;
+    CK(cudaGetLastError());
+    if ((st = run_loop(h, g, max_iter, &hs, info, s)) != SPG_OK) return st;
+    const bool out_host = !is_device_ptr(p_out);
+    float *od = p_out;
+    if (out_host) { CK(h->stage_out.ensure((size_t)N)); od = h->stage_out.p; }
+    launch_scatter_state(N, h->fwd.d_inv, h->d_state, od, nullptr, 0, s);
+    if (out_host) CK(cudaMemcpyAsync(p_out, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
+}
+
+extern "C" spg_status spg_hits(spg_handle h, int norm, double tol, int max_iter, float *auth,
+                               float *hub, spg_iter_info *info, void *stream)
+{
+    if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
+    if (h->kind != SPG_KIND_HITS) return fail(SPG_ERR_UNSUPPORTED, "hits needs a HITS handle");
+    if (!auth || !hub || (norm != 1 && norm != 2) || max_iter < 0 || tol > 0)
+        return fail(SPG_ERR_INVALID, "bad hits arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->fwd.n, n = h->n_graph;
+    spg_status st = ensure_vectors(h, N);
+    if (st != SPG_OK) return st;
+    IterState hs = make_state(h, 1.0, 0.0, max_iter, N, h->x.p, h->y.p);
+    hs.hits_norm = norm;
+    CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
+    launch_fill(N, (float)(1.0 / (double)n), h->x.p, s);
+    LoopGraph *g;
+    const int nred = (int)h->fwd.nred;
+    st = get_loop_graph(h, "hits", [&](cudaStream_t cs, unsigned long long cond) {
+        launch_parts(h, EPI_HITS, nullptr, nullptr, h->d_state, h->red.p, cs);
+        launch_check(EPI_HITS, h->d_state, h->red.p, nred, cond, 1, cs);
+    }, &g);
+    if (st != SPG_OK) return st;
+    CK(cudaGetLastError());
+    if ((st = run_loop(h, g, max_iter, &hs, info, s)) != SPG_OK) return st;
+    // normalised iterate into [auth; hub] (original order)
+    CK(h->stage_out.ensure((size_t)N));
+    launch_scatter_state(N, h->fwd.d_inv, h->d_state, h->stage_out.p, h->d_row_half, 1, s);
+    const cudaMemcpyKind ka = is_device_ptr(auth) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const cudaMemcpyKind kh = is_device_ptr(hub) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(auth, h->stage_out.p, n * sizeof(float), ka, s));
+    CK(cudaMemcpyAsync(hub, h->stage_out.p + n, n * sizeof(float), kh, s));
+    CK(cudaStreamSynchronize(s));
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds, int k,
+                              double tol, int max_iter, float *R, spg_iter_info *info,
+                              void *stream)
+{
+    if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
+    if (h->kind != SPG_KIND_PAGERANK) return fail(SPG_ERR_UNSUPPORTED, "rwr needs a PAGERANK handle");
+    if (!seeds || !R || k < 1 || k > 64 || !(restart > 0.f && restart <= 1.f) || max_iter < 0)
+        return fail(SPG_ERR_INVALID, "bad rwr arguments (1 <= k <= 64)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Layout &L = h->fwd;
+    const int64_t N = L.n;
+    std::vector<int32_t> ps((size_t)k);
+    for (int j = 0; j < k; ++j) {
+        if (seeds[j] < 0 || seeds[j] >= N) return fail(SPG_ERR_INVALID, "seed out of range");
+        ps[(size_t)j] = L.perm[(size_t)seeds[j]];
+    }
+    const double c = 1.0 - (double)restart;
+    IterState hs;
+    spg_status st;
+    LoopGraph *g;
+    const int nred = (int)L.nred;
+    if (k == 1) {
+        if ((st = ensure_vectors(h, N)) != SPG_OK) return st;
+        hs = make_state(h, c, tol, max_iter, N, h->x.p, h->y.p);
+        hs.seed = ps[0];
+        CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
+        CK(h->seeds.ensure(1));
+        CK(cudaMemcpyAsync(h->seeds.p, ps.data(), sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(h->x.p, 0, N * sizeof(float), s));
+        launch_set_one(h->x.p, h->seeds.p, 1, s);
+        launch_init_delta(h->d_state, s);
+        st = get_loop_graph(h, "rwr1", [&](cudaStream_t cs, unsigned long long cond) {
+            launch_parts(h, EPI_RWR, nullptr, nullptr, h->d_state, h->red.p, cs);
+            launch_check(EPI_RWR, h->d_state, h->red.p, nred, cond, 1, cs);
+        }, &g);
+        if (st != SPG_OK) return st;
+        CK(cudaGetLastError());
+        if ((st = run_loop(h, g, max_iter, &hs, info, s)) != SPG_OK) return st;
+        const bool out_host = !is_device_ptr(R);
+        float *od = R;
+        if (out_host) { CK(h->stage_out.ensure((size_t)N)); od = h->stage_out.p; }
+        launch_scatter_state(N, L.d_inv, h->d_state, od, nullptr, 0, s);
+        if (out_host) CK(cudaMemcpyAsync(R, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
+    }
+    // k restart vectors as one SpMM per iteration
+    CK(h->X.ensure((size_t)(N * k)));
+    CK(h->Y.ensure((size_t)(N * k)));
+    CK(h->partial_k.ensure((size_t)std::max<int64_t>(1, L.nchunk_slots) * k));
+    CK(h->redk.ensure((size_t)std::max<int64_t>(1, L.nred) * 2 * k));
+    CK(h->delta_k.ensure((size_t)k));
+    CK(h->l1_k.ensure((size_t)k));
+    CK(h->seeds.ensure((size_t)k));
+    hs = make_state(h, c, tol, max_iter, N, h->X.p, h->Y.p);
+    CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->seeds.p, ps.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    launch_onehot_rows(N, k, h->seeds.p, h->X.p, s);
+    launch_init_delta_k(h->d_state, h->X.p, k, h->delta_k.p, s);
+    SplitView sv = L.split_view();
+    sv.partial = h->partial_k.p;
+    const std::string key = "rwrk" + std::to_string(k);
+    st = get_loop_graph(h, key, [&](cudaStream_t cs, unsigned long long cond) {
+        for (const PartView &pv : views_of(L))
+            launch_part_spmm(EPI_RWR, pv, sv, nullptr, nullptr, k, h->d_state, h->seeds.p,
+                             h->delta_k.p, h->redk.p, cs);
+        launch_check_k(h->d_state, h->redk.p, nred, k, h->delta_k.p, h->l1_k.p, cond, 1, cs);
+    }, &g);
+    if (st != SPG_OK) return st;
+    CK(cudaGetLastError());
+    if ((st = run_loop(h, g, max_iter, &hs, info, s)) != SPG_OK) return st;
+    const bool out_host = !is_device_ptr(R);
+    float *cur = hs.buf[hs.parity];
+    if (out_host) {
+        CK(h->stage_out.ensure((size_t)(N * k)));
+        launch_scatter_rows(N, k, L.d_inv, cur, h->stage_out.p, k, 1.f, 0.f, s);
+        CK(cudaMemcpyAsync(R, h->stage_out.p, N * k * sizeof(float), cudaMemcpyDeviceToHost, s));
+    } else {
+        launch_scatter_rows(N, k, L.d_inv, cur, R, k, 1.f, 0.f, s);
+    }
+    CK(cudaStreamSynchronize(s));
+    return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
+}
+
+// ------------------------------------------------------------ baselines --
+
+extern "C" spg_status spg_baseline_spmv(spg_handle h, spg_baseline which, const float *x, float *y,
+                                        float alpha, float beta, void *stream)
+{
+    if (!h || !h->d_rp) return fail(SPG_ERR_INVALID, "baselines need keep_csr");
+    if (!x || !y || !is_device_ptr(x) || !is_device_ptr(y)) return fail(SPG_ERR_INVALID, "device vectors");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = h->n_graph;
+    CK(h->y.ensure((size_t)n));
+    if (which == SPG_BASELINE_CSR_SCALAR)
+        launch_csr_scalar(EPI_RAW, n, h->d_rp, h->d_col, h->d_val, h->d_dangling, x, h->y.p, nullptr, nullptr, nullptr, s);
+    else
+        launch_csr_vector(EPI_RAW, n, h->d_rp, h->d_col, h->d_val, h->d_dangling, x, h->y.p, nullptr, nullptr, nullptr, s);
+    launch_scatter_axpby(n, nullptr, h->y.p, y, alpha, beta, s);
+    CK(cudaGetLastError());
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_baseline_pagerank(spg_handle h, spg_baseline which, float damping,
+                                            double tol, int max_iter, float *p_out,
+                                            spg_iter_info *info, void *stream)
+{
+    if (!h || !h->d_rp || h->kind != SPG_KIND_PAGERANK) return fail(SPG_ERR_INVALID, "baselines need a PAGERANK handle with keep_csr");
+    if (!p_out || max_iter < 0) return fail(SPG_ERR_INVALID, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = h->n_graph;
+    spg_status st = ensure_vectors(h, n);
+    if (st != SPG_OK) return st;
+    const int nb = which == SPG_BASELINE_CSR_SCALAR ? csr_scalar_blocks(n) : csr_vector_blocks(n);
+    CK(h->red.ensure((size_t)nb));
+    IterState hs = make_state(h, damping, tol, max_iter, n, h->x.p, h->y.p);
+    CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
+    launch_fill(n, (float)(1.0 / (double)n), h->x.p, s);
+    launch_init_delta_flags(h->d_state, h->d_dangling, s);
+    LoopGraph *g;
+    const std::string key = which == SPG_BASELINE_CSR_SCALAR ? "pr_csr_scalar" : "pr_csr_vector";
+    st = get_loop_graph(h, key, [&](cudaStream_t cs, unsigned long long cond) {
+        if (which == SPG_BASELINE_CSR_SCALAR)
+            launch_csr_scalar(EPI_PAGERANK, n, h->d_rp, h->d_col, h->d_val, h->d_dangling, nullptr, nullptr, h->d_state, h->red.p, nullptr, cs);
+        else
+            launch_csr_vector(EPI_PAGERANK, n, h->d_rp, h->d_col, h->d_val, h->d_dangling, nullptr, nullptr, h->d_state, h->red.p, nullptr, cs);
+        launch_check(EPI_PAGERANK, h->d_state, h->red.p, nb, cond, 1, cs);
+    }, &g);
+    if (st != SPG_OK) return st;
+    CK(cudaGetLastError());
+    if ((st = run_loop(h, g, max_iter, &hs, info, s)) != SPG_OK) return st;
+    float *cur = hs.buf[hs.parity];
+    const cudaMemcpyKind kd = is_device_ptr(p_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(p_out, cur, n * sizeof(float), kd, s));
+    CK(cudaStreamSynchronize(s));
+    return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
+}
+
+extern "C" spg_status spg_time_parts(spg_handle h, int mode, int reps, float *ms_out, void *stream)
+{
+    if (!h || h->host_only || !ms_out || reps < 1 || (mode != 0 && mode != 1))
+        return fail(SPG_ERR_INVALID, "bad arguments");
+    if (mode == 1 && (h->kind != SPG_KIND_PAGERANK || !h->x.p)) return fail(SPG_ERR_INVALID, "run spg_pagerank first");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->fwd.n;
+    spg_status st = ensure_vectors(h, N);
+    if (st != SPG_OK) return st;
+    if (mode == 0) CK(cudaMemsetAsync(h->x.p, 0, N * sizeof(float), s));
+    const SplitView sv = h->fwd.split_view();
+    const std::vector<PartView> pvs = views_of(h->fwd);
+    for (size_t p = 0; p < pvs.size(); ++p) {
+        CK(cudaEventRecord(h->ev0, s));
+        for (int r = 0; r < reps; ++r) {
+            if (mode == 0) launch_part(EPI_RAW, pvs[p], sv, h->x.p, h->y.p, nullptr, nullptr, s);
+            else launch_part(EPI_PAGERANK, pvs[p], sv, nullptr, nullptr, h->d_state, h->red.p, s);
+        }
+        CK(cudaEventRecord(h->ev1, s));
+        CK(cudaEventSynchronize(h->ev1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        ms_out[p] = ms / (float)reps;
+    }
+    CK(cudaGetLastError());
+    return SPG_OK;
+}
+
+// --------------------------------------------------- not yet available --
+
+extern "C" spg_status spg_set_edge_logits(spg_handle h, const float *theta, void *stream)
+{
+    (void)h; (void)theta; (void)stream;
+    return fail(SPG_ERR_UNSUPPORTED, "edge logits not built yet");
+}
+
+extern "C" spg_status spg_rwr_weighted(spg_handle h, float restart, int32_t seed, double tol,
+                                       int max_iter, float *r, spg_iter_info *info, void *stream)
+{
+    (void)h; (void)restart; (void)seed; (void)tol; (void)max_iter; (void)r; (void)info; (void)stream;
+    return fail(SPG_ERR_UNSUPPORTED, "weighted rwr not built yet");
+}
+
+extern "C" spg_status spg_rwr_adjoint(spg_handle h, float restart, int32_t seed, const float *r,
+                                      const float *g, double tol, int max_iter, float *lambda,
+                                      float *dtheta, spg_iter_info *info, void *stream)
+{
+    (void)h; (void)restart; (void)seed; (void)r; (void)g; (void)tol; (void)max_iter;
+    (void)lambda; (void)dtheta; (void)info; (void)stream;
+    return fail(SPG_ERR_UNSUPPORTED, "adjoint not built yet");
+}
+
+extern "C" spg_status spg_batch_pagerank(const spg_handle *graphs, int count, float damping,
+                                         double tol, int max_iter, float *const *p_out,
+                                         spg_iter_info *info, void *stream)
+{
+    (void)graphs; (void)count; (void)damping; (void)tol; (void)max_iter; (void)p_out;
+    (void)info; (void)stream;
+    return fail(SPG_ERR_UNSUPPORTED, "batched pagerank not built yet");
+}
+
+// ------------------------------------------------------------------ misc --
+
+extern "C" spg_status spg_load_table(const char *path)
+{
+    if (!path) { perf_table_default(perf_table()); return SPG_OK; }
+    std::string err;
+    PerfTable t;
+    if (!perf_table_load(path, t, err)) return fail(SPG_ERR_INVALID, err);
+    perf_table() = t;
+    return SPG_OK;
+}
+
+extern "C" int64_t spg_launch_count(void) { return launch_count(); }
+
+extern "C" const char *spg_status_string(spg_status s)
+{
+    switch (s) {
+    case SPG_OK: return "ok";
+    case SPG_NOT_CONVERGED: return "not converged";
+    case SPG_ERR_INVALID: return "invalid argument";
+    case SPG_ERR_OOM: return "out of memory";
+    case SPG_ERR_CUDA: return "CUDA error";
+    case SPG_ERR_TIMEOUT: return "device wait timed out";
+    case SPG_ERR_UNSUPPORTED: return "unsupported for this handle";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *spg_last_error(void) { return g_err.c_str(); }
+extern "C" const char *spg_version(void) { return "spg 0.1 (sm_103a)"; }

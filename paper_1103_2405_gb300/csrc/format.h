@@ -1,0 +1,149 @@
+// format.h -- host-side description of a built tiled composite layout.
+#pragma once
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "spg_internal.h"
+
+namespace spg {
+
+// Performance lookup table of Section 3.3: slots/s for (major, log2 w_pad,
+// log2 h_pad) buckets, each log clamped to [0, kTableLog).
+constexpr int kTableLog = 21;
+struct PerfTable {
+    double perf[2][kTableLog][kTableLog];
+    bool loaded = false;
+};
+PerfTable &perf_table();                // process-wide table
+void perf_table_default(PerfTable &t);  // built-in analytic table
+bool perf_table_load(const char *path, PerfTable &t, std::string &err);
+double perf_lookup(const PerfTable &t, int major, int64_t wpad, int64_t hpad);
+
+struct BuildParams {
+    int64_t tile_width = 0;   // resolved (> 0) or <= 0 for none
+    int64_t wl = 0;
+    int64_t heavy = -1;
+    int layout_rule = 1;
+    int64_t max_warps = 9728;
+    double split_cost = 2e-7;
+    bool keep_plan = false;
+    bool track_edges = false;
+};
+
+struct PartHost {
+    int64_t c0 = 0, c1 = 0;
+    int64_t heavy = 0, wl = 0, nnz = 0, nvirt = 0;
+    int64_t nwl = 0;          // regular workloads
+    int64_t nwl_total = 0;    // + zero-row workloads
+    int64_t wl_off = 0;       // first workload in the concatenated array
+    int32_t nblocks = 0, red_base = 0;
+    double predicted_s = 0;
+    // plan (keep_plan)
+    std::vector<int32_t> rank_row, rank_chunk, rank_len;
+    std::vector<int64_t> wl_first;
+    std::vector<int32_t> wl_h, wl_w, wl_major;
+};
+
+struct Layout {
+    int64_t n = 0, nnz = 0;
+    int64_t tile_width = 0, ntile = 0;
+    int64_t max_warps = 0;
+    int64_t padded_slots = 0;
+    int64_t nsplit = 0, nchunk_slots = 0, nred = 0;
+    int64_t dangling_start = 0;
+    std::vector<int32_t> perm, inv;
+    std::vector<PartHost> parts;
+    std::vector<int64_t> zero_rows;
+    // packed arrays (host copy; released after upload unless kept)
+    std::vector<Workload> wl;
+    std::vector<uint32_t> rows;
+    std::vector<uint2> slab;
+    std::vector<SplitRow> split;
+    std::vector<int32_t> slot_owner;
+    std::vector<int64_t> edge_slot;     // edge id -> slab slot (track_edges)
+    // device copies
+    int32_t *d_perm = nullptr, *d_inv = nullptr;
+    Workload *d_wl = nullptr;
+    uint32_t *d_rows = nullptr;
+    uint2 *d_slab = nullptr;
+    SplitRow *d_split = nullptr;
+    int32_t *d_slot_owner = nullptr;
+    float *d_partial = nullptr;
+    uint32_t *d_counter = nullptr;
+    int64_t *d_edge_slot = nullptr;
+    int64_t device_bytes = 0;
+    bool on_device = false;
+
+    std::vector<PartView> part_views() const;
+    SplitView split_view() const;
+    void free_device();
+};
+
+// X given column by column (CSC of the matrix to format): column j holds
+// entries (rowidx[k], val[k]) for k in [colptr[j], colptr[j+1]); eid[k] (or k
+// when eid is null) names the entry for the edge map.  row_class (nullable)
+// marks rows of the second HITS half.
+struct ColumnSource {
+    int64_t n = 0;
+    const int64_t *colptr = nullptr;
+    const int32_t *rowidx = nullptr;
+    const float *val = nullptr;
+    const int64_t *eid = nullptr;
+    const uint8_t *row_class = nullptr;
+};
+
+// Host builder: order, tile, rank, tune, pack.  Fills `out` (host arrays).
+bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &out,
+                  std::string &err);
+// Upload the packed arrays; release host copies unless keep_host.
+cudaError_t upload_layout(Layout &L, bool keep_host, cudaStream_t stream);
+
+// Algorithm 3 model (seconds) of one ranked part; Algorithm 2 search.
+double model_time(const int32_t *vlen, int64_t nv, int64_t WL, int64_t max_warps, int rule,
+                  const PerfTable &t);
+int64_t alg2_search(const int32_t *vlen, int64_t nv, int64_t nnz, int64_t max_warps,
+                    int rule, const PerfTable &t, double *best);
+
+int hw_threads();
+
+// Run fn(lo, hi) over [0, n) split into contiguous chunks on hw_threads()
+// threads (serially below `grain` items).
+template <class F> void parallel_for(int64_t n, int64_t grain, F fn)
+{
+    int nt = hw_threads();
+    if (n <= grain || nt <= 1) { if (n > 0) fn((int64_t)0, n); return; }
+    int64_t chunks = std::min<int64_t>(nt, (n + grain - 1) / grain);
+    std::vector<std::thread> th;
+    th.reserve((size_t)chunks);
+    for (int64_t t = 1; t < chunks; ++t)
+        th.emplace_back([=] { fn(n * t / chunks, n * (t + 1) / chunks); });
+    fn((int64_t)0, n / chunks);
+    for (auto &x : th) x.join();
+}
+
+// Dynamic version: items handed out in blocks of `block` (uneven work).
+template <class F> void parallel_dynamic(int64_t n, int64_t block, F fn)
+{
+    int nt = hw_threads();
+    if (n <= block || nt <= 1) { if (n > 0) fn((int64_t)0, n); return; }
+    std::atomic<int64_t> next{0};
+    auto worker = [&] {
+        for (;;) {
+            int64_t lo = next.fetch_add(block);
+            if (lo >= n) break;
+            fn(lo, std::min(n, lo + block));
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(worker);
+    worker();
+    for (auto &x : th) x.join();
+}
+
+}  // namespace spg

@@ -1,0 +1,905 @@
+// kernels.cu -- sm_103a kernels of the tiled composite SpMV/SpMM and the
+// power-iteration epilogues (Yang, Parthasarathy, Sadayappan: Section 3.1
+// Solution 3 for the workload kernels, Appendix F Eqs. 6-9 for the epilogues,
+// Appendix B for the plain CSR-scalar / CSR-vector baselines).
+//
+// Design on GB300: the gather of x is the only reused stream, so x goes
+// through the read-only path (__ldg: L1 + L2) and the matrix slots stream
+// with evict-first loads (__ldcs) so they do not displace x.  One warp owns
+// one workload; row-major workloads reduce with warp shuffles (tree order),
+// column-major ones keep one row per lane.  No atomics touch y: every row has
+// exactly one writer per part; rows cut into chunks are combined by the last
+// chunk to finish, summing the chunk partials in chunk order (deterministic).
+// No tensor cores: the gather is not a dense contraction.
+#include <atomic>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace spg {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t k) { g_launches.fetch_add(k); }
+int64_t launch_count() { return g_launches.load(); }
+
+constexpr unsigned kFull = 0xffffffffu;
+// Resident blocks per SM the SpMV kernel is compiled for (8 x 8 warps = the
+// SM's 64-warp limit): the gather is latency bound, so occupancy is what
+// keeps enough loads in flight.
+constexpr int kPartMinBlocks = 5;
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// One stored slot: padding has col = -1 and contributes nothing (no gather).
+__device__ __forceinline__ float slot_fma(uint2 v, const float *__restrict__ x, float acc)
+{
+    const int c = (int)v.x;
+    const float xv = c >= 0 ? __ldg(x + c) : 0.0f;
+    return fmaf(__uint_as_float(v.y), xv, acc);
+}
+
+// Uniform per-launch epilogue parameters, read once from the state.
+struct Epi {
+    float c, base, tele;
+    int seed;
+    int64_t dstart;
+    float sc[2];
+    int hnorm;
+};
+
+template <int MODE>
+__device__ __forceinline__ Epi load_epi(const IterState *st)
+{
+    Epi E;
+    E.c = 1.f; E.base = 0.f; E.tele = 0.f; E.seed = -1; E.dstart = 0;
+    E.sc[0] = E.sc[1] = 1.f; E.hnorm = 2;
+    if (MODE == EPI_PAGERANK || MODE == EPI_RWR) {
+        const double c = st->c, d = st->delta;
+        E.c = (float)c;
+        E.dstart = st->dangling_start;
+        if (MODE == EPI_PAGERANK) E.base = (float)((c * d + (1.0 - c)) * st->inv_n);
+        else { E.tele = (float)(c * d + (1.0 - c)); E.seed = st->seed; }
+    } else if (MODE == EPI_HITS) {
+        E.sc[0] = (float)st->scale[0];
+        E.sc[1] = (float)st->scale[1];
+        E.hnorm = st->hits_norm;
+    }
+    return E;
+}
+
+// Final value of row v from its total, written to y; sums for the check.
+template <int MODE>
+__device__ __forceinline__ void epilogue(const Epi &E, uint32_t rid, float tot,
+                                         const float *__restrict__ x, float *__restrict__ y,
+                                         double &r0, double &r1)
+{
+    const uint32_t v = rid & kRowIdMask;
+    if (rid & kRowNotFirst) tot += y[v];
+    if (rid & kRowNotLast) { y[v] = tot; return; }
+    if (MODE == EPI_RAW) {
+        y[v] = tot;
+    } else if (MODE == EPI_PAGERANK || MODE == EPI_RWR) {
+        float add = MODE == EPI_PAGERANK ? E.base : ((int)v == E.seed ? E.tele : 0.f);
+        float f = fmaf(E.c, tot, add);
+        y[v] = f;
+        r0 += fabs((double)f - (double)x[v]);
+        if ((int64_t)v >= E.dstart) r1 += (double)f;
+    } else {  // HITS: a-rows read the hub half and vice versa
+        const int cls = (rid & kRowClass) ? 1 : 0;
+        float f = tot * (cls ? E.sc[0] : E.sc[1]);
+        y[v] = f;
+        double q = E.hnorm == 2 ? (double)f * (double)f : (double)f;
+        if (cls == 0) r0 += q; else r1 += q;
+    }
+}
+
+// A chunk of a split row: publish the partial; the last chunk to arrive sums
+// all partials in chunk order and finishes the row.
+template <int MODE>
+__device__ __noinline__ void finish_split(const Epi &E, const SplitView &sv, double2 *red,
+                                          uint32_t rid, float acc, const float *__restrict__ x,
+                                          float *__restrict__ y)
+{
+    const int slot = (int)(rid & 0x7fffffffu);
+    sv.partial[slot] = acc;
+    __threadfence();
+    const int s = sv.slot_owner[slot];
+    const SplitRow sr = sv.rows[s];
+    const unsigned prev = atomicAdd(sv.counter + s, 1u);
+    if (prev != (unsigned)sr.nchunks - 1) return;
+    __threadfence();
+    float tot = 0.f;
+    for (int k = 0; k < sr.nchunks; ++k) tot += __ldcg(sv.partial + sr.first_slot + k);
+    sv.counter[s] = 0u;
+    double r0 = 0.0, r1 = 0.0;
+    epilogue<MODE>(E, sr.row, tot, x, y, r0, r1);
+    if (MODE != EPI_RAW) red[sr.red_slot] = make_double2(r0, r1);
+}
+
+template <int MODE>
+__device__ __forceinline__ void finish_row(const Epi &E, const SplitView &sv, double2 *red,
+                                           uint32_t rid, float acc, const float *__restrict__ x,
+                                           float *__restrict__ y, double &r0, double &r1)
+{
+    if (rid & kRowSplit) finish_split<MODE>(E, sv, red, rid, acc, x, y);
+    else epilogue<MODE>(E, rid, acc, x, y, r0, r1);
+}
+
+template <int MODE>
+__device__ __forceinline__ void block_reduce_store(double r0, double r1, double2 *out)
+{
+    __shared__ double s0[kWarpsPerBlock], s1[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    r0 = warp_sum_d(r0);
+    r1 = warp_sum_d(r1);
+    if (lane == 0) { s0[warp] = r0; s1[warp] = r1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) { a += s0[w]; b += s1[w]; }
+        *out = make_double2(a, b);
+    }
+}
+
+// Tiled composite SpMV over one part (Solution 3): warp `wid` computes
+// workload `wid`.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock, kPartMinBlocks)
+k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restrict__ yout,
+       const IterState *__restrict__ st, double2 *__restrict__ red)
+{
+    const float *x = xin;
+    float *y = yout;
+    Epi E = load_epi<MODE>(st);
+    if (st) {
+        const int par = st->parity;
+        x = st->buf[par];
+        y = st->buf[par ^ 1];
+    }
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    double r0 = 0.0, r1 = 0.0;
+    if (wid < pv.nwl) {
+        const Workload d = pv.wl[wid];
+        const uint32_t *__restrict__ rows = pv.rows + d.rows;
+        const uint2 *__restrict__ slab = pv.slab + d.slab;
+        if (d.major == 0) {
+            // row-major (CSR-vector): the warp strides across one row at a time
+            for (int i = 0; i < d.h; ++i) {
+                const uint2 *s = slab + (int64_t)i * d.w;
+                float acc = 0.f;
+                int e = lane;
+                for (; e + 96 < d.w; e += 128) {
+                    const uint2 a0 = __ldcs(s + e), a1 = __ldcs(s + e + 32);
+                    const uint2 a2 = __ldcs(s + e + 64), a3 = __ldcs(s + e + 96);
+                    acc = slot_fma(a0, x, acc);
+                    acc = slot_fma(a1, x, acc);
+                    acc = slot_fma(a2, x, acc);
+                    acc = slot_fma(a3, x, acc);
+                }
+                for (; e < d.w; e += 32) acc = slot_fma(__ldcs(s + e), x, acc);
+                acc = warp_sum(acc);
+                if (lane == 0) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc, x, y, r0, r1);
+            }
+        } else {
+            // column-major (ELL): one row per lane, 32-row blocks
+            const int hp = (d.h + 31) & ~31;
+            for (int b = 0; b < hp; b += 32) {
+                const uint2 *s = slab + (int64_t)b * d.w + lane;
+                float acc = 0.f;
+                int e = 0;
+                for (; e + 3 < d.w; e += 4) {
+                    const uint2 a0 = __ldcs(s + (int64_t)e * 32), a1 = __ldcs(s + (int64_t)(e + 1) * 32);
+                    const uint2 a2 = __ldcs(s + (int64_t)(e + 2) * 32), a3 = __ldcs(s + (int64_t)(e + 3) * 32);
+                    acc = slot_fma(a0, x, acc);
+                    acc = slot_fma(a1, x, acc);
+                    acc = slot_fma(a2, x, acc);
+                    acc = slot_fma(a3, x, acc);
+                }
+                for (; e < d.w; ++e) acc = slot_fma(__ldcs(s + (int64_t)e * 32), x, acc);
+                const int i = b + lane;
+                if (i < d.h) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc, x, y, r0, r1);
+            }
+        }
+    }
+    if (MODE != EPI_RAW) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
+}
+
+int part_blocks_per_sm()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_part<EPI_PAGERANK>, kBlock, 0) != cudaSuccess)
+        return 0;
+    return b;
+}
+
+void launch_part(int mode, const PartView &pv, const SplitView &sv, const float *x, float *y,
+                 const IterState *st, double2 *red, cudaStream_t s)
+{
+    if (pv.nblocks <= 0) return;
+    dim3 g(pv.nblocks), b(kBlock);
+    switch (mode) {
+    case EPI_RAW: k_part<EPI_RAW><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
+    case EPI_PAGERANK: k_part<EPI_PAGERANK><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
+    case EPI_RWR: k_part<EPI_RWR><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
+    default: k_part<EPI_HITS><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
+    }
+    count_launches(1);
+}
+
+// ------------------------------------------------------------------ SpMM --
+
+// Y' row v, columns [c0, c0+64) of one chunk: lane owns columns c0+2*lane,
+// c0+2*lane+1.  The row's stored entries are a prefix of its slots (padding
+// last), so a batch of 32 entries is loaded one per lane and broadcast.
+__device__ __forceinline__ uint2 ld_entry(const uint2 *slab, const Workload &d, int i, int e)
+{
+    const int64_t off = d.major == 0 ? (int64_t)i * d.w + e
+                                     : (int64_t)(i >> 5) * 32 * d.w + (int64_t)e * 32 + (i & 31);
+    return __ldcs(slab + off);
+}
+
+template <bool EVEN>
+__device__ __forceinline__ void row_spmm(const uint2 *slab, const Workload &d, int i,
+                                         const float *__restrict__ X, int k, int j0, int lane,
+                                         float &a0, float &a1)
+{
+    const int wrow = d.major == 0 ? d.w : d.w;  // entries stored per row
+    for (int e0 = 0; e0 < wrow; e0 += 32) {
+        const int e = e0 + lane;
+        uint2 ent = make_uint2(0xffffffffu, 0u);
+        if (e < wrow) ent = ld_entry(slab, d, i, e);
+        const unsigned valid = __ballot_sync(kFull, (int)ent.x >= 0);
+        const int cnt = __popc(valid);
+        int t = 0;
+        for (; t + 1 < cnt; t += 2) {
+            const int c_0 = __shfl_sync(kFull, (int)ent.x, t);
+            const float v_0 = __shfl_sync(kFull, __uint_as_float(ent.y), t);
+            const int c_1 = __shfl_sync(kFull, (int)ent.x, t + 1);
+            const float v_1 = __shfl_sync(kFull, __uint_as_float(ent.y), t + 1);
+            const float *r0p = X + (int64_t)c_0 * k, *r1p = X + (int64_t)c_1 * k;
+            if (EVEN) {
+                if (j0 < k) {
+                    const float2 p = __ldg(reinterpret_cast<const float2 *>(r0p + j0));
+                    const float2 q = __ldg(reinterpret_cast<const float2 *>(r1p + j0));
+                    a0 = fmaf(v_0, p.x, a0); a1 = fmaf(v_0, p.y, a1);
+                    a0 = fmaf(v_1, q.x, a0); a1 = fmaf(v_1, q.y, a1);
+                }
+            } else {
+                if (j0 < k) { a0 = fmaf(v_0, __ldg(r0p + j0), a0); a0 = fmaf(v_1, __ldg(r1p + j0), a0); }
+                if (j0 + 1 < k) { a1 = fmaf(v_0, __ldg(r0p + j0 + 1), a1); a1 = fmaf(v_1, __ldg(r1p + j0 + 1), a1); }
+            }
+        }
+        for (; t < cnt; ++t) {
+            const int c_0 = __shfl_sync(kFull, (int)ent.x, t);
+            const float v_0 = __shfl_sync(kFull, __uint_as_float(ent.y), t);
+            const float *r0p = X + (int64_t)c_0 * k;
+            if (EVEN) {
+                if (j0 < k) {
+                    const float2 p = __ldg(reinterpret_cast<const float2 *>(r0p + j0));
+                    a0 = fmaf(v_0, p.x, a0); a1 = fmaf(v_0, p.y, a1);
+                }
+            } else {
+                if (j0 < k) a0 = fmaf(v_0, __ldg(r0p + j0), a0);
+                if (j0 + 1 < k) a1 = fmaf(v_0, __ldg(r0p + j0 + 1), a1);
+            }
+        }
+        if (cnt < 32) break;
+    }
+}
+
+struct EpiK {
+    float c;
+    int64_t dstart;
+};
+
+// Row epilogue for SpMM: RAW or RWR per column (restart seeds[j], dangling
+// mass delta_k[j]).  Per-lane sums for its two columns.
+template <int MODE>
+__device__ __forceinline__ void epilogue_k(const EpiK &E, uint32_t rid, float t0, float t1,
+                                           int j0, int k, const float *__restrict__ X,
+                                           float *__restrict__ Y, const int32_t *seeds,
+                                           const double *delta_k, double *acc4)
+{
+    const uint32_t v = rid & kRowIdMask;
+    float *yr = Y + (int64_t)v * k;
+    const float *xr = X + (int64_t)v * k;
+    const bool h0 = j0 < k, h1 = j0 + 1 < k;
+    if (rid & kRowNotFirst) { if (h0) t0 += yr[j0]; if (h1) t1 += yr[j0 + 1]; }
+    if ((rid & kRowNotLast) || MODE == EPI_RAW) {
+        if (h0) yr[j0] = t0;
+        if (h1) yr[j0 + 1] = t1;
+        return;
+    }
+    const double c = E.c;
+    if (h0) {
+        float add = (int)v == __ldg(seeds + j0) ? (float)(c * delta_k[j0] + (1.0 - c)) : 0.f;
+        float f = fmaf(E.c, t0, add);
+        yr[j0] = f;
+        acc4[0] += fabs((double)f - (double)xr[j0]);
+        if ((int64_t)v >= E.dstart) acc4[2] += f;
+    }
+    if (h1) {
+        float add = (int)v == __ldg(seeds + j0 + 1) ? (float)(c * delta_k[j0 + 1] + (1.0 - c)) : 0.f;
+        float f = fmaf(E.c, t1, add);
+        yr[j0 + 1] = f;
+        acc4[1] += fabs((double)f - (double)xr[j0 + 1]);
+        if ((int64_t)v >= E.dstart) acc4[3] += f;
+    }
+}
+
+// SpMM over one part.  Split rows: chunk partials (k floats per chunk slot)
+// in sv.partial, combined in chunk order by the last chunk.  Per-block
+// column sums for RWR into redk[(slot * 2 + q) * k + j] (q = 0: L1, 1: dangling).
+template <int MODE, bool EVEN>
+__global__ void __launch_bounds__(kBlock)
+k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__restrict__ Yout,
+            int k, const IterState *__restrict__ st, const int32_t *__restrict__ seeds,
+            const double *__restrict__ delta_k, double *__restrict__ redk)
+{
+    const float *X = Xin;
+    float *Y = Yout;
+    EpiK E;
+    E.c = 1.f;
+    E.dstart = 0;
+    if (st) {
+        const int par = st->parity;
+        X = st->buf[par];
+        Y = st->buf[par ^ 1];
+        E.c = (float)st->c;
+        E.dstart = st->dangling_start;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wid = blockIdx.x * kWarpsPerBlock + warp;
+    double acc4[4] = {0.0, 0.0, 0.0, 0.0};   // L1 j0, L1 j0+1, dangling j0, dangling j0+1
+    if (wid < pv.nwl) {
+        const Workload d = pv.wl[wid];
+        const uint2 *slab = pv.slab + d.slab;
+        for (int i = 0; i < d.h; ++i) {
+            const uint32_t rid = __ldg(pv.rows + d.rows + i);
+            for (int c0 = 0; c0 < k; c0 += 64) {
+                const int j0 = c0 + 2 * lane;
+                float a0 = 0.f, a1 = 0.f;
+                if (d.w > 0) row_spmm<EVEN>(slab, d, i, X, k, j0, lane, a0, a1);
+                if (rid & kRowSplit) {
+                    const int slot = (int)(rid & 0x7fffffffu);
+                    float *pp = sv.partial + (int64_t)slot * k;
+                    if (j0 < k) pp[j0] = a0;
+                    if (j0 + 1 < k) pp[j0 + 1] = a1;
+                    if (c0 + 64 < k) continue;   // publish after the last column chunk
+                    __threadfence();
+                    __syncwarp();
+                    const int s = sv.slot_owner[slot];
+                    const SplitRow sr = sv.rows[s];
+                    unsigned prev = 0;
+                    if (lane == 0) prev = atomicAdd(sv.counter + s, 1u);
+                    prev = __shfl_sync(kFull, prev, 0);
+                    if (prev != (unsigned)sr.nchunks - 1) continue;
+                    __threadfence();
+                    double sr4[4] = {0.0, 0.0, 0.0, 0.0};
+                    for (int cc = 0; cc < k; cc += 64) {
+                        const int jj = cc + 2 * lane;
+                        float t0 = 0.f, t1 = 0.f;
+                        for (int q = 0; q < sr.nchunks; ++q) {
+                            const float *src = sv.partial + (int64_t)(sr.first_slot + q) * k;
+                            if (jj < k) t0 += __ldcg(src + jj);
+                            if (jj + 1 < k) t1 += __ldcg(src + jj + 1);
+                        }
+                        epilogue_k<MODE>(E, sr.row, t0, t1, jj, k, X, Y, seeds, delta_k, sr4);
+                    }
+                    if (lane == 0) sv.counter[s] = 0u;
+                    if (MODE != EPI_RAW && j0 < k) {
+                        double *o = redk + (int64_t)sr.red_slot * 2 * k;
+                        o[j0] = sr4[0];
+                        o[k + j0] = sr4[2];
+                        if (j0 + 1 < k) { o[j0 + 1] = sr4[1]; o[k + j0 + 1] = sr4[3]; }
+                    }
+                } else {
+                    epilogue_k<MODE>(E, rid, a0, a1, j0, k, X, Y, seeds, delta_k, acc4);
+                }
+            }
+        }
+    }
+    if (MODE != EPI_RAW) {
+        // per-block column sums (k <= 64 for the RWR epilogue)
+        __shared__ double sm[kWarpsPerBlock][4][32];
+        sm[warp][0][lane] = acc4[0]; sm[warp][1][lane] = acc4[1];
+        sm[warp][2][lane] = acc4[2]; sm[warp][3][lane] = acc4[3];
+        __syncthreads();
+        if (threadIdx.x < 128) {
+            const int q = threadIdx.x >> 5, l = threadIdx.x & 31;
+            double a = 0.0;
+            for (int w = 0; w < kWarpsPerBlock; ++w) a += sm[w][q][l];
+            const int j = 2 * l + (q & 1);
+            if (j < k) {
+                double *o = redk + (int64_t)(pv.red_base + blockIdx.x) * 2 * k;
+                o[(q >> 1) * k + j] = a;
+            }
+        }
+    }
+}
+
+void launch_part_spmm(int mode, const PartView &pv, const SplitView &sv, const float *X, float *Y,
+                      int k, const IterState *st, const int32_t *seeds, const double *delta_k,
+                      double *redk, cudaStream_t s)
+{
+    if (pv.nblocks <= 0) return;
+    dim3 g(pv.nblocks), b(kBlock);
+    const bool even = (k % 2) == 0;
+    if (mode == EPI_RAW) {
+        if (even) k_part_spmm<EPI_RAW, true><<<g, b, 0, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
+        else k_part_spmm<EPI_RAW, false><<<g, b, 0, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
+    } else {
+        if (even) k_part_spmm<EPI_RWR, true><<<g, b, 0, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
+        else k_part_spmm<EPI_RWR, false><<<g, b, 0, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
+    }
+    count_launches(1);
+}
+
+// ----------------------------------------------------------------- check --
+
+__device__ __forceinline__ void block_sum2_1024(double &a, double &b)
+{
+    __shared__ double s0[32], s1[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    if (lane == 0) { s0[warp] = a; s1[warp] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) { x += s0[w]; y += s1[w]; }
+        a = x;
+        b = y;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+k_check(int mode, IterState *st, const double2 *__restrict__ red, int nred,
+        cudaGraphConditionalHandle cond, int use_cond)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nred; i += blockDim.x) {
+        const double2 v = red[i];
+        a += v.x;
+        b += v.y;
+    }
+    block_sum2_1024(a, b);
+    if (threadIdx.x == 0) {
+        if (mode == EPI_HITS) {
+            const double na = st->hits_norm == 2 ? sqrt(a) : a;
+            const double nh = st->hits_norm == 2 ? sqrt(b) : b;
+            st->scale[0] = na > 0.0 ? 1.0 / na : 0.0;
+            st->scale[1] = nh > 0.0 ? 1.0 / nh : 0.0;
+            st->l1 = 0.0;
+        } else {
+            st->l1 = a;
+            st->delta = b;
+        }
+        st->iter += 1;
+        st->parity ^= 1;
+        const int done = st->iter >= st->max_iter ||
+                         (mode != EPI_HITS && st->tol > 0.0 && st->l1 < st->tol);
+        st->done = done;
+        if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
+    }
+}
+
+void launch_check(int mode, IterState *st, const double2 *red, int nred,
+                  unsigned long long cond, int use_cond, cudaStream_t s)
+{
+    k_check<<<1, 1024, 0, s>>>(mode, st, red, nred, (cudaGraphConditionalHandle)cond, use_cond);
+    count_launches(1);
+}
+
+// Per-column sums over slots for k columns (k <= 64): thread (q, part)
+// sums slots part, part+P, ... of column q in order, then parts in order.
+__global__ void __launch_bounds__(1024)
+k_check_k(IterState *st, const double *__restrict__ redk, int nred, int k, double *delta_k,
+          double *l1_k, cudaGraphConditionalHandle cond, int use_cond)
+{
+    __shared__ double part_sum[1024];
+    __shared__ double colmax[64];
+    const int Q = 2 * k;
+    const int P = blockDim.x / Q;
+    const int q = threadIdx.x % Q, p = threadIdx.x / Q;
+    double a = 0.0;
+    if (p < P)
+        for (int i = p; i < nred; i += P) a += redk[(int64_t)i * Q + q];
+    part_sum[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x < Q) {
+        double t = 0.0;
+        for (int pp = 0; pp < P; ++pp) t += part_sum[pp * Q + threadIdx.x];
+        if (threadIdx.x < k) { l1_k[threadIdx.x] = t; colmax[threadIdx.x] = t; }
+        else delta_k[threadIdx.x - k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int j = 0; j < k; ++j) m = fmax(m, colmax[j]);
+        st->l1 = m;
+        st->iter += 1;
+        st->parity ^= 1;
+        const int done = st->iter >= st->max_iter || (st->tol > 0.0 && m < st->tol);
+        st->done = done;
+        if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
+    }
+}
+
+void launch_check_k(IterState *st, const double *redk, int nred, int k, double *delta_k,
+                    double *l1_k, unsigned long long cond, int use_cond, cudaStream_t s)
+{
+    k_check_k<<<1, 1024, 0, s>>>(st, redk, nred, k, delta_k, l1_k,
+                                 (cudaGraphConditionalHandle)cond, use_cond);
+    count_launches(1);
+}
+
+__global__ void __launch_bounds__(1024) k_init_delta(IterState *st)
+{
+    const float *x = st->buf[st->parity];
+    double a = 0.0, b = 0.0;
+    for (int64_t v = st->dangling_start + threadIdx.x; v < st->n; v += blockDim.x) a += x[v];
+    block_sum2_1024(a, b);
+    if (threadIdx.x == 0) st->delta = a;
+}
+
+void launch_init_delta(IterState *st, cudaStream_t s)
+{
+    k_init_delta<<<1, 1024, 0, s>>>(st);
+    count_launches(1);
+}
+
+__global__ void __launch_bounds__(1024) k_init_delta_flags(IterState *st, const uint8_t *dangling)
+{
+    const float *x = st->buf[st->parity];
+    double a = 0.0, b = 0.0;
+    for (int64_t v = threadIdx.x; v < st->n; v += blockDim.x)
+        if (dangling[v]) a += x[v];
+    block_sum2_1024(a, b);
+    if (threadIdx.x == 0) st->delta = a;
+}
+
+void launch_init_delta_flags(IterState *st, const uint8_t *dangling, cudaStream_t s)
+{
+    k_init_delta_flags<<<1, 1024, 0, s>>>(st, dangling);
+    count_launches(1);
+}
+
+__global__ void k_set_one(float *p, const int32_t *idx, int count)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) p[idx[i]] = 1.f;
+}
+
+void launch_set_one(float *p, const int32_t *idx, int count, cudaStream_t s)
+{
+    k_set_one<<<(count + 255) / 256, 256, 0, s>>>(p, idx, count);
+    count_launches(1);
+}
+
+__global__ void __launch_bounds__(1024)
+k_init_delta_k(const IterState *st, const float *__restrict__ X, int k, double *delta_k)
+{
+    __shared__ double part_sum[1024];
+    const int P = blockDim.x / k;
+    const int j = threadIdx.x % k, p = threadIdx.x / k;
+    double a = 0.0;
+    if (p < P)
+        for (int64_t v = st->dangling_start + p; v < st->n; v += P) a += X[v * k + j];
+    part_sum[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double t = 0.0;
+        for (int pp = 0; pp < P; ++pp) t += part_sum[pp * k + threadIdx.x];
+        delta_k[threadIdx.x] = t;
+    }
+}
+
+void launch_init_delta_k(const IterState *st, const float *X, int k, double *delta_k,
+                         cudaStream_t s)
+{
+    k_init_delta_k<<<1, 1024, 0, s>>>(st, X, k, delta_k);
+    count_launches(1);
+}
+
+// ------------------------------------------------------------- vectors --
+
+static inline int grid_for(int64_t n, int per = 256)
+{
+    int64_t g = (n + per - 1) / per;
+    if (g > 152 * 64) g = 152 * 64;
+    return (int)(g > 0 ? g : 1);
+}
+
+__global__ void k_gather(int64_t n, const int32_t *__restrict__ inv, const float *__restrict__ x,
+                         float *__restrict__ xp)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        xp[i] = __ldg(x + inv[i]);
+}
+
+void launch_gather(int64_t n, const int32_t *inv, const float *x, float *xp, cudaStream_t s)
+{
+    k_gather<<<grid_for(n), 256, 0, s>>>(n, inv, x, xp);
+    count_launches(1);
+}
+
+__global__ void k_gather_rows(int64_t n, int k, const int32_t *__restrict__ inv,
+                              const float *__restrict__ X, int64_t ldx, float *__restrict__ Xp)
+{
+    const int64_t total = n * k;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k, j = t % k;
+        Xp[t] = __ldg(X + (int64_t)inv[i] * ldx + j);
+    }
+}
+
+void launch_gather_rows(int64_t n, int k, const int32_t *inv, const float *X, int64_t ldx,
+                        float *Xp, cudaStream_t s)
+{
+    k_gather_rows<<<grid_for(n * k), 256, 0, s>>>(n, k, inv, X, ldx, Xp);
+    count_launches(1);
+}
+
+__global__ void k_scatter_axpby(int64_t n, const int32_t *__restrict__ inv,
+                                const float *__restrict__ yp, float *__restrict__ y, float alpha,
+                                float beta)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = inv ? (int64_t)inv[i] : i;
+        const float v = alpha * yp[i];
+        y[o] = beta != 0.f ? fmaf(beta, y[o], v) : v;
+    }
+}
+
+void launch_scatter_axpby(int64_t n, const int32_t *inv, const float *yp, float *y, float alpha,
+                          float beta, cudaStream_t s)
+{
+    k_scatter_axpby<<<grid_for(n), 256, 0, s>>>(n, inv, yp, y, alpha, beta);
+    count_launches(1);
+}
+
+__global__ void k_scatter_rows(int64_t n, int k, const int32_t *__restrict__ inv,
+                               const float *__restrict__ Yp, float *__restrict__ Y, int64_t ldy,
+                               float alpha, float beta)
+{
+    const int64_t total = n * k;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k, j = t % k;
+        float *dst = Y + (int64_t)inv[i] * ldy + j;
+        const float v = alpha * Yp[t];
+        *dst = beta != 0.f ? fmaf(beta, *dst, v) : v;
+    }
+}
+
+void launch_scatter_rows(int64_t n, int k, const int32_t *inv, const float *Yp, float *Y,
+                         int64_t ldy, float alpha, float beta, cudaStream_t s)
+{
+    k_scatter_rows<<<grid_for(n * k), 256, 0, s>>>(n, k, inv, Yp, Y, ldy, alpha, beta);
+    count_launches(1);
+}
+
+__global__ void k_scatter_state(int64_t n, const int32_t *__restrict__ inv,
+                                const IterState *__restrict__ st, float *__restrict__ out,
+                                const uint8_t *__restrict__ row_half, int hits)
+{
+    const float *z = st->buf[st->parity];
+    float sc0 = 1.f, sc1 = 1.f;
+    if (hits) { sc0 = (float)st->scale[0]; sc1 = (float)st->scale[1]; }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float v = z[i];
+        if (hits) v *= row_half[i] ? sc1 : sc0;
+        out[inv[i]] = v;
+    }
+}
+
+void launch_scatter_state(int64_t n, const int32_t *inv, const IterState *st, float *out,
+                          const uint8_t *row_half, int hits, cudaStream_t s)
+{
+    k_scatter_state<<<grid_for(n), 256, 0, s>>>(n, inv, st, out, row_half, hits);
+    count_launches(1);
+}
+
+__global__ void k_fill(int64_t n, float v, float *__restrict__ p)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+void launch_fill(int64_t n, float v, float *p, cudaStream_t s)
+{
+    k_fill<<<grid_for(n), 256, 0, s>>>(n, v, p);
+    count_launches(1);
+}
+
+__global__ void k_onehot_rows(int64_t n, int k, const int32_t *__restrict__ seeds,
+                              float *__restrict__ X)
+{
+    const int64_t total = n * k;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k, j = t % k;
+        X[t] = (int64_t)seeds[j] == i ? 1.f : 0.f;
+    }
+}
+
+void launch_onehot_rows(int64_t n, int k, const int32_t *seeds, float *X, cudaStream_t s)
+{
+    k_onehot_rows<<<grid_for(n * k), 256, 0, s>>>(n, k, seeds, X);
+    count_launches(1);
+}
+
+// ------------------------------------------------------------ baselines --
+
+template <int MODE>
+__device__ __forceinline__ void csr_epilogue(const Epi &E, int64_t v, float acc,
+                                             const uint8_t *dangling, const float *x, float *y,
+                                             double &r0, double &r1)
+{
+    if (MODE == EPI_RAW) { y[v] = acc; return; }
+    const float f = fmaf(E.c, acc, E.base);
+    y[v] = f;
+    r0 += fabs((double)f - (double)x[v]);
+    if (dangling[v]) r1 += (double)f;
+}
+
+// Appendix B CSR kernel: one thread per row.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_csr_scalar(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+             const float *__restrict__ val, const uint8_t *__restrict__ dangling,
+             const float *__restrict__ xin, float *__restrict__ yout,
+             const IterState *__restrict__ st, double2 *__restrict__ red)
+{
+    const float *x = xin;
+    float *y = yout;
+    Epi E = load_epi<MODE>(st);
+    if (st) { x = st->buf[st->parity]; y = st->buf[st->parity ^ 1]; }
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double r0 = 0.0, r1 = 0.0;
+    if (v < n) {
+        float acc = 0.f;
+        for (int64_t k = rp[v]; k < rp[v + 1]; ++k) acc = fmaf(val[k], __ldg(x + col[k]), acc);
+        csr_epilogue<MODE>(E, v, acc, dangling, x, y, r0, r1);
+    }
+    if (MODE != EPI_RAW) block_reduce_store<MODE>(r0, r1, red + blockIdx.x);
+}
+
+// Appendix B CSR-vector kernel: one warp per row.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_csr_vector(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+             const float *__restrict__ val, const uint8_t *__restrict__ dangling,
+             const float *__restrict__ xin, float *__restrict__ yout,
+             const IterState *__restrict__ st, double2 *__restrict__ red)
+{
+    const float *x = xin;
+    float *y = yout;
+    Epi E = load_epi<MODE>(st);
+    if (st) { x = st->buf[st->parity]; y = st->buf[st->parity ^ 1]; }
+    const int lane = threadIdx.x & 31;
+    const int64_t v = blockIdx.x * (int64_t)kWarpsPerBlock + (threadIdx.x >> 5);
+    double r0 = 0.0, r1 = 0.0;
+    if (v < n) {
+        float acc = 0.f;
+        for (int64_t k = rp[v] + lane; k < rp[v + 1]; k += 32) acc = fmaf(val[k], __ldg(x + col[k]), acc);
+        acc = warp_sum(acc);
+        if (lane == 0) csr_epilogue<MODE>(E, v, acc, dangling, x, y, r0, r1);
+    }
+    if (MODE != EPI_RAW) block_reduce_store<MODE>(r0, r1, red + blockIdx.x);
+}
+
+int csr_scalar_blocks(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
+int csr_vector_blocks(int64_t n) { return (int)((n + kWarpsPerBlock - 1) / kWarpsPerBlock); }
+
+void launch_csr_scalar(int mode, int64_t n, const int64_t *rp, const int32_t *col,
+                       const float *val, const uint8_t *dangling, const float *x, float *y,
+                       const IterState *st, double2 *red, int *nblocks_out, cudaStream_t s)
+{
+    const int g = csr_scalar_blocks(n);
+    if (nblocks_out) *nblocks_out = g;
+    if (mode == EPI_RAW) k_csr_scalar<EPI_RAW><<<g, kBlock, 0, s>>>(n, rp, col, val, dangling, x, y, st, red);
+    else k_csr_scalar<EPI_PAGERANK><<<g, kBlock, 0, s>>>(n, rp, col, val, dangling, x, y, st, red);
+    count_launches(1);
+}
+
+void launch_csr_vector(int mode, int64_t n, const int64_t *rp, const int32_t *col,
+                       const float *val, const uint8_t *dangling, const float *x, float *y,
+                       const IterState *st, double2 *red, int *nblocks_out, cudaStream_t s)
+{
+    const int g = csr_vector_blocks(n);
+    if (nblocks_out) *nblocks_out = g;
+    if (mode == EPI_RAW) k_csr_vector<EPI_RAW><<<g, kBlock, 0, s>>>(n, rp, col, val, dangling, x, y, st, red);
+    else k_csr_vector<EPI_PAGERANK><<<g, kBlock, 0, s>>>(n, rp, col, val, dangling, x, y, st, red);
+    count_launches(1);
+}
+
+// ------------------------------------------------------ differentiable RWR --
+
+// Softmax of the logits over each node's out-edges (one warp per node),
+// written into the packed slots of the forward and transposed layouts.
+__global__ void k_edge_softmax(int64_t n, const int64_t *__restrict__ rp,
+                               const float *__restrict__ theta, const int64_t *__restrict__ es,
+                               uint2 *slab, const int64_t *__restrict__ est, uint2 *slab_t,
+                               float *__restrict__ P)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t b = rp[u], e = rp[u + 1];
+        if (b == e) continue;
+        float m = -INFINITY;
+        for (int64_t q = b + lane; q < e; q += 32) m = fmaxf(m, theta[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+        float sum = 0.f;
+        for (int64_t q = b + lane; q < e; q += 32) sum += __expf(theta[q] - m);
+        sum = warp_sum(sum);
+        const float inv = 1.f / sum;
+        for (int64_t q = b + lane; q < e; q += 32) {
+            const float p = __expf(theta[q] - m) * inv;
+            if (P) P[q] = p;
+            if (es) slab[es[q]].y = __float_as_uint(p);
+            if (est) slab_t[est[q]].y = __float_as_uint(p);
+        }
+    }
+}
+
+void launch_edge_softmax(int64_t n, const int64_t *a_rp, const float *theta,
+                         const int64_t *edge_slot, uint2 *slab, const int64_t *edge_slot_t,
+                         uint2 *slab_t, float *P_out, cudaStream_t s)
+{
+    k_edge_softmax<<<grid_for(n * 32), 256, 0, s>>>(n, a_rp, theta, edge_slot, slab, edge_slot_t,
+                                                    slab_t, P_out);
+    count_launches(1);
+}
+
+__global__ void k_edge_grad(int64_t n, const int64_t *__restrict__ rp,
+                            const int32_t *__restrict__ col, const float *__restrict__ P,
+                            const float *__restrict__ lam, const float *__restrict__ r, float c,
+                            float *__restrict__ dth)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t b = rp[u], e = rp[u + 1];
+        if (b == e) continue;
+        const float cr = c * r[u];
+        float dot = 0.f;
+        for (int64_t q = b + lane; q < e; q += 32) dot = fmaf(P[q], cr * lam[col[q]], dot);
+        dot = warp_sum(dot);
+        for (int64_t q = b + lane; q < e; q += 32) dth[q] = P[q] * (cr * lam[col[q]] - dot);
+    }
+}
+
+void launch_edge_grad(int64_t n, const int64_t *a_rp, const int32_t *a_col, const float *P,
+                      const float *lambda, const float *r, float c, float *dtheta,
+                      cudaStream_t s)
+{
+    k_edge_grad<<<grid_for(n * 32), 256, 0, s>>>(n, a_rp, a_col, P, lambda, r, c, dtheta);
+    count_launches(1);
+}
+
+}  // namespace spg

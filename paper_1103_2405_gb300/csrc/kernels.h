@@ -1,0 +1,89 @@
+// kernels.h -- host launchers of the sm_103a kernels (kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "spg_internal.h"
+
+namespace spg {
+
+// Epilogue of the last part that touches a row (Appendix F).
+enum EpiMode {
+    EPI_RAW = 0,       // y' = (M' x')_v
+    EPI_PAGERANK = 1,  // y' = c (M' x')_v + (c delta + 1 - c)/n;  sum |y'-x'|, dangling sum
+    EPI_RWR = 2,       // y' = c (M' x')_v + [v == s](c delta + 1 - c); same sums
+    EPI_HITS = 3       // y' = (M' x')_v * scale[other half];  per-half sum or sum of squares
+};
+
+// One tiled-composite launch of one part (Solution 3: one warp per
+// workload).  x/y come from st->buf[parity] when st != nullptr.
+void launch_part(int mode, const PartView &pv, const SplitView &sv, const float *x, float *y,
+                 const IterState *st, double2 *red, cudaStream_t s);
+
+// SpMM over one part: Y' (n x k, ld k) += rows of M' X' (k <= 1024).  Modes
+// EPI_RAW and EPI_RWR (per-column restart seeds, per-column sums into
+// red[(slot * 2 + {0,1}) * k + j]).
+void launch_part_spmm(int mode, const PartView &pv, const SplitView &sv, const float *X, float *Y,
+                      int k, const IterState *st, const int32_t *seeds, const double *delta_k,
+                      double *redk, cudaStream_t s);
+
+// Sum the reduction slots and advance the iteration state (one block).
+// mode EPI_PAGERANK / EPI_RWR: l1 = sum slot.x, delta = sum slot.y;
+// EPI_HITS: scale[c] = 1/norm of half c.  Sets the graph conditional
+// (when cond != 0) to "keep iterating".
+void launch_check(int mode, IterState *st, const double2 *red, int nred,
+                  unsigned long long cond, int use_cond, cudaStream_t s);
+// Same for SpMM RWR: per-column l1_k / delta_k, l1 = max over columns.
+void launch_check_k(IterState *st, const double *redk, int nred, int k, double *delta_k,
+                    double *l1_k, unsigned long long cond, int use_cond, cudaStream_t s);
+
+// Dangling mass of buf[parity] (positions >= dangling_start) into st->delta.
+void launch_init_delta(IterState *st, cudaStream_t s);
+void launch_init_delta_flags(IterState *st, const uint8_t *dangling, cudaStream_t s);
+// p[idx[i]] = 1 for i < count
+void launch_set_one(float *p, const int32_t *idx, int count, cudaStream_t s);
+void launch_init_delta_k(const IterState *st, const float *X, int k, double *delta_k,
+                         cudaStream_t s);
+
+// Permutation and vector helpers.
+void launch_gather(int64_t n, const int32_t *inv, const float *x, float *xp, cudaStream_t s);
+void launch_gather_rows(int64_t n, int k, const int32_t *inv, const float *X, int64_t ldx,
+                        float *Xp, cudaStream_t s);
+void launch_scatter_axpby(int64_t n, const int32_t *inv, const float *yp, float *y, float alpha,
+                          float beta, cudaStream_t s);
+void launch_scatter_rows(int64_t n, int k, const int32_t *inv, const float *Yp, float *Y,
+                         int64_t ldy, float alpha, float beta, cudaStream_t s);
+// out[inv[k]] = buf[parity][k] * (scale of k's half when hits) from state
+void launch_scatter_state(int64_t n, const int32_t *inv, const IterState *st, float *out,
+                          const uint8_t *row_half, int hits, cudaStream_t s);
+void launch_fill(int64_t n, float v, float *p, cudaStream_t s);
+void launch_onehot_rows(int64_t n, int k, const int32_t *seeds, float *X, cudaStream_t s);
+
+// Plain CSR baselines on M in original order.  mode EPI_RAW or EPI_PAGERANK
+// (dangling flags per row; reductions into red[blockIdx]).
+void launch_csr_scalar(int mode, int64_t n, const int64_t *rp, const int32_t *col,
+                       const float *val, const uint8_t *dangling, const float *x, float *y,
+                       const IterState *st, double2 *red, int *nblocks_out, cudaStream_t s);
+void launch_csr_vector(int mode, int64_t n, const int64_t *rp, const int32_t *col,
+                       const float *val, const uint8_t *dangling, const float *x, float *y,
+                       const IterState *st, double2 *red, int *nblocks_out, cudaStream_t s);
+int csr_scalar_blocks(int64_t n);
+int csr_vector_blocks(int64_t n);
+
+// Edge weights: P_e = softmax over out-edges of theta, written to the slab
+// slots edge_slot[e] (forward) and edge_slot_t[e] (transposed, nullable).
+void launch_edge_softmax(int64_t n, const int64_t *a_rp, const float *theta,
+                         const int64_t *edge_slot, uint2 *slab, const int64_t *edge_slot_t,
+                         uint2 *slab_t, float *P_out, cudaStream_t s);
+// dtheta_e = P_e (G_e - sum_{e' in out(u)} P_e' G_e'), G_e = c lambda_v r_u.
+void launch_edge_grad(int64_t n, const int64_t *a_rp, const int32_t *a_col, const float *P,
+                      const float *lambda, const float *r, float c, float *dtheta,
+                      cudaStream_t s);
+
+// Resident blocks per SM of the tiled-composite SpMV kernel on this device.
+int part_blocks_per_sm();
+
+// Launch counter of this library.
+void count_launches(int64_t k);
+int64_t launch_count();
+
+}  // namespace spg

@@ -1,0 +1,89 @@
+// spg_internal.h -- layout of the tiled composite format shared by the host
+// builder (builder.cpp), the kernels (kernels.cu) and the C ABI (capi.cu).
+//
+// Device layout of one format (all arrays in HBM, allocated once at build):
+//   perm[n] / inv[n]   int32  symmetric order by decreasing column length
+//                             (Section 3.1, Solution 2): perm[orig] = pos.
+//   parts              ntile dense column tiles (Algorithm 1) + the sparse
+//                      remainder, launched in order (Solution 1).
+//   workloads[]        24-byte descriptors, one warp each (Solution 3).
+//   rows[]             int32 row entry per (virtual) row of a workload:
+//                      permuted row id | flag bits below.
+//   slab[]             uint2 {col, float bits} slots; padding has col = -1.
+//                      Row-major workload: row r at slab + r*w (w padded to
+//                      32).  Column-major: 32-row blocks, slot of (row r,
+//                      entry k) = slab + (r/32)*32*w + k*32 + r%32.
+//   split tables       chunks of rows longer than the heavy threshold.
+#pragma once
+#include <cstdint>
+
+namespace spg {
+
+constexpr int kWarp = 32;
+constexpr int kWarpsPerBlock = 8;          // 256-thread blocks
+constexpr int kBlock = kWarp * kWarpsPerBlock;
+constexpr int kZeroRowsPerWorkload = 1024; // rows of a w = 0 workload
+
+// Flag bits of a row entry.
+constexpr uint32_t kRowSplit = 0x80000000u;    // low 31 bits: chunk slot of a split row
+constexpr uint32_t kRowNotFirst = 0x40000000u; // the row has entries in an earlier part
+constexpr uint32_t kRowNotLast = 0x20000000u;  // the row has entries in a later part
+constexpr uint32_t kRowClass = 0x10000000u;    // HITS: the row is in the hub half
+constexpr uint32_t kRowIdMask = 0x0fffffffu;   // n < 2^28
+constexpr int64_t kMaxN = (int64_t)1 << 28;
+
+struct Workload {        // 24 bytes, one warp
+    int64_t slab;        // first slot
+    int32_t rows;        // first row entry
+    int32_t w;           // row-major: padded width; column-major: width
+    int32_t h;           // rows (unpadded)
+    int32_t major;       // 0 row-major (CSR-vector), 1 column-major (ELL)
+};
+static_assert(sizeof(Workload) == 24, "Workload layout");
+
+struct SplitRow {        // one row cut into nchunks chunks (consecutive slots)
+    uint32_t row;        // permuted row id | kRowNotFirst/NotLast/Class flags
+    int32_t first_slot;
+    int32_t nchunks;
+    int32_t red_slot;    // reduction slot the finisher writes
+};
+
+// Per-part device view handed to the kernels.
+struct PartView {
+    const Workload *wl;
+    const uint32_t *rows;
+    const uint2 *slab;
+    int32_t nwl;          // workloads incl. zero-row ones
+    int32_t nblocks;      // launch blocks
+    int32_t red_base;     // first reduction slot of this part's blocks
+    int32_t pad_;
+};
+
+// Split-row scratch shared by all parts of a format.
+struct SplitView {
+    const SplitRow *rows;      // by split row index
+    const int32_t *slot_owner; // chunk slot -> split row index
+    float *partial;            // chunk slot -> partial sum (scratch)
+    uint32_t *counter;         // split row -> chunks done (scratch, kept at 0 between launches)
+};
+
+// Scalars of a power iteration, in device memory (FP64 where the sums need it).
+struct IterState {
+    double c;             // damping
+    double tol;
+    double delta;         // dangling mass of the current iterate
+    double l1;            // L1 change of the last iteration
+    double scale[2];      // HITS: factors that normalise the current iterate's halves
+    double inv_n;
+    int32_t iter;
+    int32_t max_iter;
+    int32_t parity;       // current iterate is buf[parity]
+    int32_t done;
+    int32_t seed;         // RWR restart node (permuted id)
+    int32_t hits_norm;    // 1 or 2
+    int64_t n;
+    int64_t dangling_start;
+    float *buf[2];        // ping-pong iterates (permuted order)
+};
+
+}  // namespace spg

@@ -1,0 +1,158 @@
+"""C-ABI library on the CPU: it loads, exports every symbol include/spg.h
+declares, rejects malformed input, and its host builder reproduces the
+oracle's format plan exactly (integer work, bit-exact): degree order,
+Algorithm 1 tiles, heavy-row threshold, Algorithm 2 workload size, row
+ranking and workloads (Section 3.1 Solutions 2-3, Section 3.3), and the
+packed slots hold exactly the non-zeros of M = W^T."""
+import ctypes
+import os
+import re
+import tempfile
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def spg():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_1103_2405_gb300 as m
+    return m
+
+
+def _header_symbols():
+    text = open(os.path.join(ROOT, "include", "spg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(spg):
+    L = spg.lib()
+    syms = _header_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(L, s), s
+    assert sorted(spg.EXPORTS) == syms
+    assert spg.version().startswith("spg")
+
+
+def _table_file(perf, nlog=21):
+    fd, path = tempfile.mkstemp(suffix=".txt")
+    os.close(fd)
+    with open(path, "w") as f:
+        for mj in range(2):
+            for lw in range(nlog):
+                for lh in range(nlog):
+                    f.write(f"{mj} {lw} {lh} {float(perf[(mj * nlog + lw) * nlog + lh])!r}\n")
+    return path
+
+
+CASES = [  # (scale, ef, tile_width, heavy, rule, max_warps)
+    (12, 8, 256, -1, 1, 300),
+    (12, 8, 64, 0, 0, 97),
+    (12, 8, -1, -1, 1, 9728),
+    (12, 8, 1024, 64, 1, 50),
+    (10, 16, 128, -1, 0, 13),
+]
+
+
+@pytest.mark.parametrize("scale,ef,tw,heavy,rule,mw", CASES)
+def test_host_plan_matches_oracle(spg, scale, ef, tw, heavy, rule, mw):
+    nlog = 21
+    perf = np.random.default_rng(scale * 7 + mw).uniform(1e9, 5e9, 2 * nlog * nlog)
+    path = _table_file(perf)
+    try:
+        rp, col = graphgen.rmat(scale, ef, seed=1)
+        f = spg.Format(rp, col, kind="pagerank", tile_width=tw, heavy_row=heavy, layout_rule=rule,
+                       max_warps=mw, keep_plan=True, host_only=True, table=path)
+        plan = oracle.plan_format(rp, col, tile_width=max(tw, 0), max_warps=mw,
+                                  table=(nlog, perf), heavy=heavy, rule=rule, split_cost=2e-7)
+    finally:
+        spg.load_table(None)
+        os.unlink(path)
+    pi, inv = f.perm()
+    assert np.array_equal(pi, plan["pi"]) and np.array_equal(inv, plan["inv"])
+    assert f.info()["ntile"] == plan["ntile"]
+    for p, (c0, c1, H, part) in enumerate(plan["tiles"]):
+        ti = f.tile_info(p)
+        ex = f.export_plan(p)
+        assert (ti["col_begin"], ti["col_end"]) == (c0, c1)
+        assert ex["heavy"] == H and ex["WL"] == part["WL"]
+        for k in ("rank_row", "rank_chunk", "rank_len", "wl_first", "wl_h", "wl_w", "wl_major"):
+            assert np.array_equal(ex[k], part[k]), (p, k)
+    assert np.array_equal(f.zero_rows(), plan["zero_rows"])
+    # the packed slots hold exactly M's entries (values bit-exact)
+    r, c, v = f.export_entries()
+    mrp, mcol, mval = oracle.build_M(rp, col)
+    n = rp.shape[0] - 1
+    got = np.lexsort((c, r))
+    want = np.lexsort((mcol, np.repeat(np.arange(n), np.diff(mrp))))
+    assert np.array_equal(r[got], np.repeat(np.arange(n), np.diff(mrp))[want])
+    assert np.array_equal(c[got], mcol[want])
+    assert np.array_equal(v[got].view(np.uint32), mval[want].view(np.uint32))
+
+
+def test_hits_block_matrix_entries(spg):
+    rp, col = graphgen.rmat(9, 8, seed=2)
+    n = rp.shape[0] - 1
+    f = spg.Format(rp, col, kind="hits", host_only=True, max_warps=64)
+    r, c, v = f.export_entries()
+    assert f.n == 2 * n and np.all(v == 1.0)
+    src = np.repeat(np.arange(n), np.diff(rp))
+    # Eq. 8: rows v < n hold (v, n+u) for u->v; rows n+u hold (n+u, v)
+    want = set(zip(col.tolist(), (n + src).tolist())) | set(zip((n + src).tolist(), col.tolist()))
+    assert set(zip(r.tolist(), c.tolist())) == want and len(r) == 2 * len(col)
+
+
+@pytest.mark.parametrize("bad", ["nonsquare", "rowptr0", "decreasing", "colrange", "nnz"])
+def test_malformed_csr_rejected(spg, bad):
+    rp = np.array([0, 2, 3, 3], np.int64)
+    col = np.array([1, 2, 0], np.int32)
+    L = spg.lib()
+    n, nc, nnz = 3, 3, 3
+    if bad == "nonsquare":
+        nc = 4
+    elif bad == "rowptr0":
+        rp = np.array([1, 2, 3, 3], np.int64)
+    elif bad == "decreasing":
+        rp = np.array([0, 2, 1, 3], np.int64)
+    elif bad == "colrange":
+        col = np.array([1, 3, 0], np.int32)
+    elif bad == "nnz":
+        nnz = 4
+        col = np.array([1, 2, 0, 0], np.int32)
+    csr = spg._Csr(n, nc, nnz, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(col.ctypes.data),
+                   None, 0)
+    opts = spg._Opts(0, 0, -1, 1, 64, 1, 0, 0, 0, -1, 0.0, None)
+    h = ctypes.c_void_p()
+    st = L.spg_build_format(ctypes.byref(csr), 1, ctypes.byref(opts), None, ctypes.byref(h))
+    assert st == -1 and not h.value
+    assert len(L.spg_last_error()) > 0
+
+
+def test_degenerate_graphs_build(spg):
+    # no edges at all; a single node; every row a zero row
+    for rp, col in [(np.zeros(5, np.int64), np.zeros(0, np.int32)),
+                    (np.zeros(2, np.int64), np.zeros(0, np.int32))]:
+        f = spg.Format(rp, col, kind="pagerank", host_only=True, max_warps=64)
+        info = f.info()
+        assert info["nnz"] == 0 and info["zero_rows"] == rp.shape[0] - 1
+        assert info["dangling_start"] == 0
+        r, c, v = f.export_entries()
+        assert r.size == 0
+
+
+def test_bad_table_rejected(spg):
+    fd, path = tempfile.mkstemp(suffix=".txt")
+    with os.fdopen(fd, "w") as f:
+        f.write("0 3 4 -1.0\n")
+    with pytest.raises(spg.SpgError):
+        spg.load_table(path)
+    os.unlink(path)
+    spg.load_table(None)
