@@ -118,6 +118,10 @@ typedef struct {
     /* Path of a performance table (text, see spg_load_table) or NULL for the
      * table built into the library. */
     const char *tune_table_path;
+    /* Columns of x staged in shared memory per part (the part's densest
+     * ones; the GB300 counterpart of the paper's texture-cache tile):
+     * 0 = auto (49152, i.e. 192 KB), < 0 = off (x gathered through L1/L2). */
+    int64_t x_stage_cols;
 } spg_build_opts;
 
 /* Per-call results of the power iterations. */

@@ -42,7 +42,7 @@ class _Opts(ctypes.Structure):
                 ("layout_rule", ctypes.c_int), ("max_warps", ctypes.c_int), ("vec_width", ctypes.c_int),
                 ("build_transpose", ctypes.c_int), ("keep_plan", ctypes.c_int),
                 ("keep_csr", ctypes.c_int), ("device", ctypes.c_int), ("split_cost", ctypes.c_double),
-                ("tune_table_path", ctypes.c_char_p)]
+                ("tune_table_path", ctypes.c_char_p), ("x_stage_cols", ctypes.c_int64)]
 
 
 class IterInfo(ctypes.Structure):
@@ -190,7 +190,8 @@ class Format:
 
     def __init__(self, rowptr, col, val=None, kind="pagerank", tile_width=0, wl=0, heavy_row=-1,
                  layout_rule=1, max_warps=0, vec_width=1, build_transpose=False, keep_plan=False,
-                 keep_csr=False, host_only=False, split_cost=0.0, table=None, stream=None):
+                 keep_csr=False, host_only=False, split_cost=0.0, table=None, x_stage_cols=0,
+                 stream=None):
         L = lib()
         self._h = ctypes.c_void_p(None)
         on_dev = _is_torch(rowptr) and rowptr.is_cuda
@@ -209,7 +210,7 @@ class Format:
         opts = _Opts(int(tile_width), int(wl), int(heavy_row), int(layout_rule), int(max_warps),
                      int(vec_width), int(bool(build_transpose)), int(bool(keep_plan)),
                      int(bool(keep_csr)), -1 if host_only else 0, float(split_cost),
-                     None if tpath is None else str(tpath).encode())
+                     None if tpath is None else str(tpath).encode(), int(x_stage_cols))
         _check(L.spg_build_format(ctypes.byref(csr), KIND[kind], ctypes.byref(opts),
                                   _stream(stream), ctypes.byref(self._h)))
         self.kind = kind

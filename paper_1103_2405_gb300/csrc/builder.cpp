@@ -515,7 +515,7 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
             s.row = flags;
             s.first_slot = (int32_t)L.nchunk_slots;
             s.nchunks = nch;
-            s.red_slot = (int32_t)(nblocks_all + (int64_t)L.split.size());
+            s.red_slot = (int32_t)L.split.size();
             split_first[p][(size_t)r] = s.first_slot;
             for (int32_t c = 0; c < nch; ++c) L.slot_owner.push_back((int32_t)L.split.size());
             L.split.push_back(s);
@@ -523,7 +523,7 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
         }
     }
     L.nsplit = (int64_t)L.split.size();
-    L.nred = nblocks_all + L.nsplit;
+    L.nred = nblocks_all + L.nsplit;   // with the plain 8-warp launch
 
     // workload descriptors + row entries + slab
     for (int64_t p = 0; p < P; ++p) {
@@ -694,6 +694,9 @@ std::vector<PartView> Layout::part_views() const
         pv.nwl = (int32_t)ph.nwl_total;
         pv.nblocks = ph.nblocks;
         pv.red_base = ph.red_base;
+        pv.c0 = (int32_t)ph.c0;
+        pv.xs_cols = 0;
+        pv.sched = nullptr;
         pv.pad_ = 0;
         v.push_back(pv);
     }
@@ -707,6 +710,8 @@ SplitView Layout::split_view() const
     s.slot_owner = d_slot_owner;
     s.partial = d_partial;
     s.counter = d_counter;
+    s.red_split_base = 0;
+    s.pad_ = 0;
     return s;
 }
 

@@ -99,6 +99,15 @@ struct spg_format_t {
     DevBuf<int32_t> seeds;
     DevBuf<float> X, Y;
     IterState *d_state = nullptr;
+    // launch views of the parts: plain (8-warp blocks) and staged (x slice in smem)
+    struct Views {
+        std::vector<PartView> v;
+        int32_t nblk = 0;
+        bool built = false;
+    } vplain, vstaged;
+    DevBuf<uint32_t> sched;      // staged-kernel counters, 2 per part (zero between launches)
+    int64_t stage_cols = kStagedMaxCols;
+    int num_sms = 152;
     std::map<std::string, LoopGraph> graphs;
     uint64_t epoch = 0;          // workspace generation the cached graphs were built for
     uint64_t graphs_epoch = 0;
@@ -131,6 +140,7 @@ struct spg_format_t {
         cudaFree(d_rp); cudaFree(d_col); cudaFree(d_val); cudaFree(d_dangling);
         cudaFree(d_row_half); cudaFree(d_arp); cudaFree(d_acol); cudaFree(d_P);
         x.release(); y.release(); stage_in.release(); stage_out.release(); red.release();
+        sched.release();
         redk.release(); delta_k.release(); l1_k.release(); partial_k.release(); seeds.release();
         X.release(); Y.release();
         cudaFree(d_state);
@@ -369,6 +379,10 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
             if (e == cudaErrorMemoryAllocation) return fail(SPG_ERR_OOM, "device memory for the format");
             if (e != cudaSuccess) return cuda_fail(e, "upload");
             const int64_t N = h->fwd.n;
+            cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+            h->stage_cols = o.x_stage_cols < 0 ? 0 : (o.x_stage_cols > 0 ? std::min<int64_t>(o.x_stage_cols, kStagedMaxCols) : kStagedMaxCols);
+            CK(h->sched.ensure(2 * h->fwd.parts.size()));
+            CK(cudaMemset(h->sched.p, 0, 2 * h->fwd.parts.size() * sizeof(uint32_t)));
             CK(cudaMalloc((void **)&h->d_state, sizeof(IterState)));
             CK(cudaEventCreate(&h->ev0));
             CK(cudaEventCreate(&h->ev1));
@@ -552,13 +566,61 @@ extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, in
 
 // ---------------------------------------------------------------- drivers --
 
-static std::vector<PartView> views_of(const Layout &L) { return L.part_views(); }
+// Launch views of the forward layout.  Staged: parts at least 1024 columns
+// wide get the persistent kernel with min(stage_cols, width) columns of x in
+// shared memory, one block per SM; the rest (and every part when staging is
+// off) get 8-warp blocks, one warp per workload.  Block reduction slots are
+// laid out part after part; split rows reduce after all blocks.
+static spg_format_t::Views &get_views(spg_handle h, bool staged)
+{
+    staged = staged && h->stage_cols > 0;
+    spg_format_t::Views &V = staged ? h->vstaged : h->vplain;
+    if (V.built) return V;
+    const Layout &L = h->fwd;
+    int32_t base = 0;
+    V.v.clear();
+    for (size_t p = 0; p < L.parts.size(); ++p) {
+        const PartHost &ph = L.parts[p];
+        PartView pv;
+        std::memset(&pv, 0, sizeof pv);
+        pv.wl = L.d_wl + ph.wl_off;
+        pv.rows = L.d_rows;
+        pv.slab = L.d_slab;
+        pv.sched = h->sched.p + 2 * p;
+        pv.nwl = (int32_t)ph.nwl_total;
+        pv.c0 = (int32_t)ph.c0;
+        const int64_t width = ph.c1 - ph.c0;
+        if (staged && width >= 1024 && ph.nwl_total > 0) {
+            pv.xs_cols = (int32_t)std::min<int64_t>(h->stage_cols, width);
+            pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
+        } else {
+            pv.xs_cols = 0;
+            pv.nblocks = (int32_t)((ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        }
+        pv.red_base = base;
+        base += pv.nblocks;
+        V.v.push_back(pv);
+    }
+    V.nblk = base;
+    V.built = true;
+    return V;
+}
+
+static SplitView split_of(spg_handle h, const spg_format_t::Views &V)
+{
+    SplitView sv = h->fwd.split_view();
+    sv.red_split_base = V.nblk;
+    return sv;
+}
+
+static int nred_of(spg_handle h, const spg_format_t::Views &V) { return V.nblk + (int)h->fwd.nsplit; }
 
 static spg_status ensure_vectors(spg_handle h, int64_t N)
 {
     CK(h->x.ensure((size_t)N));
     CK(h->y.ensure((size_t)N));
-    CK(h->red.ensure((size_t)std::max<int64_t>(1, h->fwd.nred)));
+    const int nr = std::max(nred_of(h, get_views(h, true)), nred_of(h, get_views(h, false)));
+    CK(h->red.ensure((size_t)std::max(1, nr)));
     return SPG_OK;
 }
 
@@ -576,8 +638,9 @@ static spg_status device_in(spg_handle h, const float *p, int64_t count, const f
 static void launch_parts(spg_handle h, int mode, const float *x, float *y, const IterState *st,
                          double2 *red, cudaStream_t s)
 {
-    const SplitView sv = h->fwd.split_view();
-    for (const PartView &pv : views_of(h->fwd)) launch_part(mode, pv, sv, x, y, st, red, s);
+    const spg_format_t::Views &V = get_views(h, true);
+    const SplitView sv = split_of(h, V);
+    for (const PartView &pv : V.v) launch_part(mode, pv, sv, x, y, st, red, s);
 }
 
 extern "C" spg_status spg_spmv_permuted(spg_handle h, const float *xp, float *yp, void *stream)
@@ -632,9 +695,10 @@ extern "C" spg_status spg_spmm(spg_handle h, const float *X, int64_t ldx, float 
     CK(h->Y.ensure((size_t)(N * k)));
     CK(h->partial_k.ensure((size_t)std::max<int64_t>(1, L.nchunk_slots) * k));
     launch_gather_rows(N, k, L.d_inv, X, ldx, h->X.p, s);
-    SplitView sv = L.split_view();
+    const spg_format_t::Views &V = get_views(h, false);
+    SplitView sv = split_of(h, V);
     sv.partial = h->partial_k.p;
-    for (const PartView &pv : views_of(L))
+    for (const PartView &pv : V.v)
         launch_part_spmm(EPI_RAW, pv, sv, h->X.p, h->Y.p, k, nullptr, nullptr, nullptr, nullptr, s);
     launch_scatter_rows(N, k, L.d_inv, h->Y.p, Y, ldy, alpha, beta, s);
     CK(cudaGetLastError());
@@ -754,7 +818,7 @@ extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int 
     }
     launch_init_delta(h->d_state, s);
     LoopGraph *g;
-    const int nred = (int)h->fwd.nred;
+    const int nred = nred_of(h, get_views(h, true));
     st = get_loop_graph(h, "pagerank", [&](cudaStream_t cs, unsigned long long cond) {
         launch_parts(h, EPI_PAGERANK, nullptr, nullptr, h->d_state, h->red.p, cs);
         launch_check(EPI_PAGERANK, h->d_state, h->red.p, nred, cond, 1, cs);
@@ -787,7 +851,7 @@ extern "C" spg_status spg_hits(spg_handle h, int norm, double tol, int max_iter,
     CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
     launch_fill(N, (float)(1.0 / (double)n), h->x.p, s);
     LoopGraph *g;
-    const int nred = (int)h->fwd.nred;
+    const int nred = nred_of(h, get_views(h, true));
     st = get_loop_graph(h, "hits", [&](cudaStream_t cs, unsigned long long cond) {
         launch_parts(h, EPI_HITS, nullptr, nullptr, h->d_state, h->red.p, cs);
         launch_check(EPI_HITS, h->d_state, h->red.p, nred, cond, 1, cs);
@@ -826,7 +890,7 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
     IterState hs;
     spg_status st;
     LoopGraph *g;
-    const int nred = (int)L.nred;
+    const int nred = nred_of(h, get_views(h, true));
     if (k == 1) {
         if ((st = ensure_vectors(h, N)) != SPG_OK) return st;
         hs = make_state(h, c, tol, max_iter, N, h->x.p, h->y.p);
@@ -856,7 +920,9 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
     CK(h->X.ensure((size_t)(N * k)));
     CK(h->Y.ensure((size_t)(N * k)));
     CK(h->partial_k.ensure((size_t)std::max<int64_t>(1, L.nchunk_slots) * k));
-    CK(h->redk.ensure((size_t)std::max<int64_t>(1, L.nred) * 2 * k));
+    const spg_format_t::Views &VK = get_views(h, false);
+    const int nredk = nred_of(h, VK);
+    CK(h->redk.ensure((size_t)std::max(1, nredk) * 2 * k));
     CK(h->delta_k.ensure((size_t)k));
     CK(h->l1_k.ensure((size_t)k));
     CK(h->seeds.ensure((size_t)k));
@@ -865,14 +931,14 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
     CK(cudaMemcpyAsync(h->seeds.p, ps.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     launch_onehot_rows(N, k, h->seeds.p, h->X.p, s);
     launch_init_delta_k(h->d_state, h->X.p, k, h->delta_k.p, s);
-    SplitView sv = L.split_view();
+    SplitView sv = split_of(h, VK);
     sv.partial = h->partial_k.p;
     const std::string key = "rwrk" + std::to_string(k);
     st = get_loop_graph(h, key, [&](cudaStream_t cs, unsigned long long cond) {
-        for (const PartView &pv : views_of(L))
+        for (const PartView &pv : VK.v)
             launch_part_spmm(EPI_RWR, pv, sv, nullptr, nullptr, k, h->d_state, h->seeds.p,
                              h->delta_k.p, h->redk.p, cs);
-        launch_check_k(h->d_state, h->redk.p, nred, k, h->delta_k.p, h->l1_k.p, cond, 1, cs);
+        launch_check_k(h->d_state, h->redk.p, nredk, k, h->delta_k.p, h->l1_k.p, cond, 1, cs);
     }, &g);
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
@@ -954,8 +1020,9 @@ extern "C" spg_status spg_time_parts(spg_handle h, int mode, int reps, float *ms
     spg_status st = ensure_vectors(h, N);
     if (st != SPG_OK) return st;
     if (mode == 0) CK(cudaMemsetAsync(h->x.p, 0, N * sizeof(float), s));
-    const SplitView sv = h->fwd.split_view();
-    const std::vector<PartView> pvs = views_of(h->fwd);
+    const spg_format_t::Views &V = get_views(h, true);
+    const SplitView sv = split_of(h, V);
+    const std::vector<PartView> &pvs = V.v;
     for (size_t p = 0; p < pvs.size(); ++p) {
         CK(cudaEventRecord(h->ev0, s));
         for (int r = 0; r < reps; ++r) {

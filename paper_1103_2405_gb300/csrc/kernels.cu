@@ -28,7 +28,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // Resident blocks per SM the SpMV kernel is compiled for (8 x 8 warps = the
 // SM's 64-warp limit): the gather is latency bound, so occupancy is what
 // keeps enough loads in flight.
-constexpr int kPartMinBlocks = 5;
+constexpr int kPartMinBlocks = 6;
+// Staged variant: one 32-warp block per SM sharing up to kStagedMaxCols
+// floats (192 KB) of x in shared memory.
+constexpr int kStagedBlock = 1024;
 
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -127,7 +130,7 @@ __device__ __noinline__ void finish_split(const Epi &E, const SplitView &sv, dou
     sv.counter[s] = 0u;
     double r0 = 0.0, r1 = 0.0;
     epilogue<MODE>(E, sr.row, tot, x, y, r0, r1);
-    if (MODE != EPI_RAW) red[sr.red_slot] = make_double2(r0, r1);
+    if (MODE != EPI_RAW) red[sv.red_split_base + sr.red_slot] = make_double2(r0, r1);
 }
 
 template <int MODE>
@@ -142,7 +145,7 @@ __device__ __forceinline__ void finish_row(const Epi &E, const SplitView &sv, do
 template <int MODE>
 __device__ __forceinline__ void block_reduce_store(double r0, double r1, double2 *out)
 {
-    __shared__ double s0[kWarpsPerBlock], s1[kWarpsPerBlock];
+    __shared__ double s0[32], s1[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     r0 = warp_sum_d(r0);
     r1 = warp_sum_d(r1);
@@ -150,13 +153,100 @@ __device__ __forceinline__ void block_reduce_store(double r0, double r1, double2
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;
-        for (int w = 0; w < kWarpsPerBlock; ++w) { a += s0[w]; b += s1[w]; }
+        const int nw = blockDim.x >> 5;
+        for (int w = 0; w < nw; ++w) { a += s0[w]; b += s1[w]; }
         *out = make_double2(a, b);
     }
 }
 
-// Tiled composite SpMV over one part (Solution 3): warp `wid` computes
-// workload `wid`.
+// x gathers: straight from global memory through the read-only path, or
+// from the shared-memory copy of the part's first `S` columns (its densest
+// ones: columns are in decreasing-length order) with global fallback.
+struct GatherGlobal {
+    const float *__restrict__ x;
+    __device__ __forceinline__ float operator()(int c) const { return __ldg(x + c); }
+};
+struct GatherStaged {
+    const float *__restrict__ x;
+    const float *xs;
+    int c0;
+    unsigned S;
+    __device__ __forceinline__ float operator()(int c) const
+    {
+        const unsigned o = (unsigned)(c - c0);
+        return o < S ? xs[o] : __ldg(x + c);
+    }
+};
+
+template <class G>
+__device__ __forceinline__ float slot_fma_g(uint2 v, const G &g, float acc)
+{
+    const int c = (int)v.x;
+    const float xv = c >= 0 ? g(c) : 0.0f;
+    return fmaf(__uint_as_float(v.y), xv, acc);
+}
+
+// One workload (Solution 3) computed by the calling warp.
+template <int MODE, class G>
+__device__ __forceinline__ void do_workload(const Workload &d, const PartView &pv,
+                                            const SplitView &sv, const G &g, const Epi &E,
+                                            const float *__restrict__ x, float *__restrict__ y,
+                                            double2 *red, int lane, double &r0, double &r1)
+{
+    const uint32_t *__restrict__ rows = pv.rows + d.rows;
+    const uint2 *__restrict__ slab = pv.slab + d.slab;
+    if (d.major == 0) {
+        // row-major (CSR-vector): the warp strides across one row at a time
+        for (int i = 0; i < d.h; ++i) {
+            const uint2 *s = slab + (int64_t)i * d.w;
+            float acc = 0.f;
+            int e = lane;
+            for (; e + 96 < d.w; e += 128) {
+                const uint2 a0 = __ldcs(s + e), a1 = __ldcs(s + e + 32);
+                const uint2 a2 = __ldcs(s + e + 64), a3 = __ldcs(s + e + 96);
+                acc = slot_fma_g(a0, g, acc);
+                acc = slot_fma_g(a1, g, acc);
+                acc = slot_fma_g(a2, g, acc);
+                acc = slot_fma_g(a3, g, acc);
+            }
+            for (; e < d.w; e += 32) acc = slot_fma_g(__ldcs(s + e), g, acc);
+            acc = warp_sum(acc);
+            if (lane == 0) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc, x, y, r0, r1);
+        }
+    } else {
+        // column-major (ELL): one row per lane, 32-row blocks
+        const int hp = (d.h + 31) & ~31;
+        for (int b = 0; b < hp; b += 32) {
+            const uint2 *s = slab + (int64_t)b * d.w + lane;
+            float acc = 0.f;
+            int e = 0;
+            for (; e + 3 < d.w; e += 4) {
+                const uint2 a0 = __ldcs(s + (int64_t)e * 32), a1 = __ldcs(s + (int64_t)(e + 1) * 32);
+                const uint2 a2 = __ldcs(s + (int64_t)(e + 2) * 32), a3 = __ldcs(s + (int64_t)(e + 3) * 32);
+                acc = slot_fma_g(a0, g, acc);
+                acc = slot_fma_g(a1, g, acc);
+                acc = slot_fma_g(a2, g, acc);
+                acc = slot_fma_g(a3, g, acc);
+            }
+            for (; e < d.w; ++e) acc = slot_fma_g(__ldcs(s + (int64_t)e * 32), g, acc);
+            const int i = b + lane;
+            if (i < d.h) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc, x, y, r0, r1);
+        }
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void resolve_xy(const IterState *st, const float *&x, float *&y)
+{
+    if (st) {
+        const int par = st->parity;
+        x = st->buf[par];
+        y = st->buf[par ^ 1];
+    }
+}
+
+// Tiled composite SpMV over one part (Solution 3), one warp per workload:
+// warp `wid` computes workload `wid` (8-warp blocks, x gathered from L1/L2).
 template <int MODE>
 __global__ void __launch_bounds__(kBlock, kPartMinBlocks)
 k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restrict__ yout,
@@ -164,56 +254,59 @@ k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restri
 {
     const float *x = xin;
     float *y = yout;
-    Epi E = load_epi<MODE>(st);
-    if (st) {
-        const int par = st->parity;
-        x = st->buf[par];
-        y = st->buf[par ^ 1];
-    }
+    const Epi E = load_epi<MODE>(st);
+    resolve_xy<MODE>(st, x, y);
     const int lane = threadIdx.x & 31;
     const int wid = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     double r0 = 0.0, r1 = 0.0;
     if (wid < pv.nwl) {
-        const Workload d = pv.wl[wid];
-        const uint32_t *__restrict__ rows = pv.rows + d.rows;
-        const uint2 *__restrict__ slab = pv.slab + d.slab;
-        if (d.major == 0) {
-            // row-major (CSR-vector): the warp strides across one row at a time
-            for (int i = 0; i < d.h; ++i) {
-                const uint2 *s = slab + (int64_t)i * d.w;
-                float acc = 0.f;
-                int e = lane;
-                for (; e + 96 < d.w; e += 128) {
-                    const uint2 a0 = __ldcs(s + e), a1 = __ldcs(s + e + 32);
-                    const uint2 a2 = __ldcs(s + e + 64), a3 = __ldcs(s + e + 96);
-                    acc = slot_fma(a0, x, acc);
-                    acc = slot_fma(a1, x, acc);
-                    acc = slot_fma(a2, x, acc);
-                    acc = slot_fma(a3, x, acc);
-                }
-                for (; e < d.w; e += 32) acc = slot_fma(__ldcs(s + e), x, acc);
-                acc = warp_sum(acc);
-                if (lane == 0) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc, x, y, r0, r1);
-            }
-        } else {
-            // column-major (ELL): one row per lane, 32-row blocks
-            const int hp = (d.h + 31) & ~31;
-            for (int b = 0; b < hp; b += 32) {
-                const uint2 *s = slab + (int64_t)b * d.w + lane;
-                float acc = 0.f;
-                int e = 0;
-                for (; e + 3 < d.w; e += 4) {
-                    const uint2 a0 = __ldcs(s + (int64_t)e * 32), a1 = __ldcs(s + (int64_t)(e + 1) * 32);
-                    const uint2 a2 = __ldcs(s + (int64_t)(e + 2) * 32), a3 = __ldcs(s + (int64_t)(e + 3) * 32);
-                    acc = slot_fma(a0, x, acc);
-                    acc = slot_fma(a1, x, acc);
-                    acc = slot_fma(a2, x, acc);
-                    acc = slot_fma(a3, x, acc);
-                }
-                for (; e < d.w; ++e) acc = slot_fma(__ldcs(s + (int64_t)e * 32), x, acc);
-                const int i = b + lane;
-                if (i < d.h) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc, x, y, r0, r1);
-            }
+        const GatherGlobal g{x};
+        do_workload<MODE>(pv.wl[wid], pv, sv, g, E, x, y, red, lane, r0, r1);
+    }
+    if (MODE != EPI_RAW) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
+}
+
+// Same computation with the part's densest x columns staged in shared
+// memory: one persistent 32-warp block per SM copies x[c0, c0 + S) into
+// shared memory (the GB300 counterpart of the paper's texture-cache tile,
+// Section 3.1 Solution 1), then its warps take workloads in order from a
+// counter (pv.sched[0]); the last warp out resets the counters for the next
+// launch (pv.sched[1] counts finished warps).  No waits between blocks.
+template <int MODE>
+__global__ void __launch_bounds__(kStagedBlock, 1)
+k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
+              float *__restrict__ yout, const IterState *__restrict__ st,
+              double2 *__restrict__ red)
+{
+    extern __shared__ float xs[];
+    const float *x = xin;
+    float *y = yout;
+    const Epi E = load_epi<MODE>(st);
+    resolve_xy<MODE>(st, x, y);
+    const int S = pv.xs_cols, c0 = pv.c0;
+    if (((c0 | S) & 3) == 0) {
+        const float4 *src = reinterpret_cast<const float4 *>(x + c0);
+        float4 *dst = reinterpret_cast<float4 *>(xs);
+        for (int i = threadIdx.x; i < (S >> 2); i += blockDim.x) dst[i] = __ldg(src + i);
+    } else {
+        for (int i = threadIdx.x; i < S; i += blockDim.x) xs[i] = __ldg(x + c0 + i);
+    }
+    __syncthreads();
+    const GatherStaged g{x, xs, c0, (unsigned)S};
+    const int lane = threadIdx.x & 31;
+    double r0 = 0.0, r1 = 0.0;
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(pv.sched, 1u);
+        w = __shfl_sync(kFull, w, 0);
+        if (w >= (unsigned)pv.nwl) break;
+        do_workload<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, r0, r1);
+    }
+    if (lane == 0) {
+        const unsigned done = atomicAdd(pv.sched + 1, 1u);
+        if (done == gridDim.x * (blockDim.x >> 5) - 1) {   // every warp has left the loop
+            pv.sched[0] = 0u;
+            pv.sched[1] = 0u;
         }
     }
     if (MODE != EPI_RAW) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
@@ -227,10 +320,34 @@ int part_blocks_per_sm()
     return b;
 }
 
+template <int MODE> static void launch_staged(const PartView &pv, const SplitView &sv, const float *x,
+                                              float *y, const IterState *st, double2 *red,
+                                              cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_part_staged<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kStagedMaxCols * (int)sizeof(float));
+        attr = true;
+    }
+    k_part_staged<MODE><<<pv.nblocks, kStagedBlock, (size_t)pv.xs_cols * sizeof(float), s>>>(
+        pv, sv, x, y, st, red);
+}
+
 void launch_part(int mode, const PartView &pv, const SplitView &sv, const float *x, float *y,
                  const IterState *st, double2 *red, cudaStream_t s)
 {
     if (pv.nblocks <= 0) return;
+    if (pv.xs_cols > 0) {
+        switch (mode) {
+        case EPI_RAW: launch_staged<EPI_RAW>(pv, sv, x, y, st, red, s); break;
+        case EPI_PAGERANK: launch_staged<EPI_PAGERANK>(pv, sv, x, y, st, red, s); break;
+        case EPI_RWR: launch_staged<EPI_RWR>(pv, sv, x, y, st, red, s); break;
+        default: launch_staged<EPI_HITS>(pv, sv, x, y, st, red, s); break;
+        }
+        count_launches(1);
+        return;
+    }
     dim3 g(pv.nblocks), b(kBlock);
     switch (mode) {
     case EPI_RAW: k_part<EPI_RAW><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
@@ -403,7 +520,7 @@ k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__r
                     }
                     if (lane == 0) sv.counter[s] = 0u;
                     if (MODE != EPI_RAW && j0 < k) {
-                        double *o = redk + (int64_t)sr.red_slot * 2 * k;
+                        double *o = redk + (int64_t)(sv.red_split_base + sr.red_slot) * 2 * k;
                         o[j0] = sr4[0];
                         o[k + j0] = sr4[2];
                         if (j0 + 1 < k) { o[j0 + 1] = sr4[1]; o[k + j0 + 1] = sr4[3]; }

@@ -45,7 +45,7 @@ struct SplitRow {        // one row cut into nchunks chunks (consecutive slots)
     uint32_t row;        // permuted row id | kRowNotFirst/NotLast/Class flags
     int32_t first_slot;
     int32_t nchunks;
-    int32_t red_slot;    // reduction slot the finisher writes
+    int32_t red_slot;    // index of this split row (its reduction slot after the blocks')
 };
 
 // Per-part device view handed to the kernels.
@@ -53,11 +53,17 @@ struct PartView {
     const Workload *wl;
     const uint32_t *rows;
     const uint2 *slab;
+    uint32_t *sched;      // staged kernel: {next workload, warps done}, zero between launches
     int32_t nwl;          // workloads incl. zero-row ones
     int32_t nblocks;      // launch blocks
     int32_t red_base;     // first reduction slot of this part's blocks
+    int32_t c0;           // first column of the part
+    int32_t xs_cols;      // > 0: columns [c0, c0 + xs_cols) staged in shared memory
     int32_t pad_;
 };
+
+// Largest x slice staged in shared memory (floats): 192 KB.
+constexpr int kStagedMaxCols = 49152;
 
 // Split-row scratch shared by all parts of a format.
 struct SplitView {
@@ -65,6 +71,8 @@ struct SplitView {
     const int32_t *slot_owner; // chunk slot -> split row index
     float *partial;            // chunk slot -> partial sum (scratch)
     uint32_t *counter;         // split row -> chunks done (scratch, kept at 0 between launches)
+    int32_t red_split_base;    // split row s reduces into slot red_split_base + s
+    int32_t pad_;
 };
 
 // Scalars of a power iteration, in device memory (FP64 where the sums need it).
