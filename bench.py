@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--impl", default="spg", choices=["spg", "reference"])
     ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="iterate with direct launches (host loop) instead of the CUDA-graph "
+                         "WHILE loop, so a kernel profiler can attribute every launch")
     return ap.parse_args()
 
 
@@ -171,7 +174,7 @@ def main():
     rp, col = graph(args.workload)
     n, nnz = int(rp.shape[0] - 1), int(rp[-1])
     t0 = time.perf_counter()
-    f = spg.Format(rp, col, kind="pagerank", keep_csr=True)
+    f = spg.Format(rp, col, kind="pagerank", keep_csr=True, loop_mode=1 if args.host_loop else 0)
     build_s = time.perf_counter() - t0
     info = f.info()
     stream = torch.cuda.current_stream(dev)

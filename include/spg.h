@@ -122,6 +122,15 @@ typedef struct {
      * ones; the GB300 counterpart of the paper's texture-cache tile):
      * 0 = auto (49152, i.e. 192 KB), < 0 = off (x gathered through L1/L2). */
     int64_t x_stage_cols;
+    /* Distance, in bytes, by which each warp's bulk L2 prefetch of its slots
+     * runs ahead of their use (TMA cp.async.bulk.prefetch).  0 = auto (8 KB),
+     * < 0 = off. */
+    int64_t slab_prefetch;
+    /* 0 = power iterations inside one CUDA graph with a conditional WHILE
+     * node (default); 1 = a host loop of direct launches that polls the
+     * convergence flag every 16 iterations (the paper's structure; also what
+     * a kernel profiler can attribute launch by launch). */
+    int loop_mode;
 } spg_build_opts;
 
 /* Per-call results of the power iterations. */

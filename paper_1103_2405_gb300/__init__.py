@@ -42,7 +42,8 @@ class _Opts(ctypes.Structure):
                 ("layout_rule", ctypes.c_int), ("max_warps", ctypes.c_int), ("vec_width", ctypes.c_int),
                 ("build_transpose", ctypes.c_int), ("keep_plan", ctypes.c_int),
                 ("keep_csr", ctypes.c_int), ("device", ctypes.c_int), ("split_cost", ctypes.c_double),
-                ("tune_table_path", ctypes.c_char_p), ("x_stage_cols", ctypes.c_int64)]
+                ("tune_table_path", ctypes.c_char_p), ("x_stage_cols", ctypes.c_int64),
+                ("slab_prefetch", ctypes.c_int64), ("loop_mode", ctypes.c_int)]
 
 
 class IterInfo(ctypes.Structure):
@@ -191,7 +192,7 @@ class Format:
     def __init__(self, rowptr, col, val=None, kind="pagerank", tile_width=0, wl=0, heavy_row=-1,
                  layout_rule=1, max_warps=0, vec_width=1, build_transpose=False, keep_plan=False,
                  keep_csr=False, host_only=False, split_cost=0.0, table=None, x_stage_cols=0,
-                 stream=None):
+                 slab_prefetch=0, loop_mode=0, stream=None):
         L = lib()
         self._h = ctypes.c_void_p(None)
         on_dev = _is_torch(rowptr) and rowptr.is_cuda
@@ -210,7 +211,8 @@ class Format:
         opts = _Opts(int(tile_width), int(wl), int(heavy_row), int(layout_rule), int(max_warps),
                      int(vec_width), int(bool(build_transpose)), int(bool(keep_plan)),
                      int(bool(keep_csr)), -1 if host_only else 0, float(split_cost),
-                     None if tpath is None else str(tpath).encode(), int(x_stage_cols))
+                     None if tpath is None else str(tpath).encode(), int(x_stage_cols),
+                     int(slab_prefetch), int(loop_mode))
         _check(L.spg_build_format(ctypes.byref(csr), KIND[kind], ctypes.byref(opts),
                                   _stream(stream), ctypes.byref(self._h)))
         self.kind = kind
@@ -327,6 +329,31 @@ class Format:
                allow_not_converged=True)
         return out, info.as_dict()
 
+    # ------------------------------------------------------ differentiable RWR --
+    def set_edge_logits(self, theta, stream=None):
+        """P = softmax over each node's out-edges of theta (nnz, A's CSR order)."""
+        _check(lib().spg_set_edge_logits(self._h, _ptr(theta)[0], _stream(stream)))
+
+    def rwr_weighted(self, seed, restart=0.15, tol=1e-10, max_iter=2000, out=None, like=None,
+                     stream=None):
+        out = _empty_like_vec(like if like is not None else np.empty(0), self.n) if out is None else out
+        info = IterInfo()
+        _check(lib().spg_rwr_weighted(self._h, float(restart), int(seed), float(tol), int(max_iter),
+                                      _ptr(out)[0], ctypes.byref(info), _stream(stream)),
+               allow_not_converged=True)
+        return out, info.as_dict()
+
+    def rwr_adjoint(self, seed, r, g, restart=0.15, tol=1e-10, max_iter=2000, lam=None, dtheta=None,
+                    stream=None):
+        """lambda = c K^T lambda + g and dL/dtheta (see spg_rwr_adjoint)."""
+        lam = _empty_like_vec(r, self.n) if lam is None else lam
+        dtheta = _empty_like_vec(r, self.nnz_in) if dtheta is None else dtheta
+        info = IterInfo()
+        _check(lib().spg_rwr_adjoint(self._h, float(restart), int(seed), _ptr(r)[0], _ptr(g)[0],
+                                     float(tol), int(max_iter), _ptr(lam)[0], _ptr(dtheta)[0],
+                                     ctypes.byref(info), _stream(stream)), allow_not_converged=True)
+        return lam, dtheta, info.as_dict()
+
     def baseline_spmv(self, which, x, y=None, alpha=1.0, beta=0.0, stream=None):
         if y is None:
             y = _empty_like_vec(x, self.n)
@@ -349,3 +376,44 @@ class Format:
                                            int(max_iter), _ptr(out)[0], ctypes.byref(info),
                                            _stream(stream)), allow_not_converged=True)
         return out, info.as_dict()
+
+
+def _autograd():
+    import torch
+
+    class RWRStationary(torch.autograd.Function):
+        """r(theta): stationary RWR vector with softmax edge weights.
+
+        forward: P = edge softmax of theta written into the format, r = the
+        RWR fixed point (spg_rwr_weighted).  backward: the adjoint fixed point
+        lambda = c K^T lambda + dL/dr on the stored transposed layout and the
+        softmax chain rule (spg_rwr_adjoint); no iterate is checkpointed."""
+
+        @staticmethod
+        def forward(ctx, theta, fmt, seed, restart=0.15, tol=1e-10, max_iter=2000):
+            fmt.set_edge_logits(theta.detach().contiguous())
+            r, _ = fmt.rwr_weighted(seed, restart, tol, max_iter, like=theta)
+            ctx.fmt, ctx.seed, ctx.restart, ctx.tol, ctx.max_iter = fmt, seed, restart, tol, max_iter
+            ctx.save_for_backward(r)
+            return r
+
+        @staticmethod
+        def backward(ctx, grad_r):
+            (r,) = ctx.saved_tensors
+            _, dth, _ = ctx.fmt.rwr_adjoint(ctx.seed, r, grad_r.contiguous(), ctx.restart, ctx.tol,
+                                            ctx.max_iter)
+            return dth, None, None, None, None, None
+
+    return RWRStationary
+
+
+_rwr_fn = None
+
+
+def __getattr__(name):
+    global _rwr_fn
+    if name == "RWRStationary":
+        if _rwr_fn is None:
+            _rwr_fn = _autograd()
+        return _rwr_fn
+    raise AttributeError(name)

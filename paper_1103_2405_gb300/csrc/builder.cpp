@@ -697,7 +697,7 @@ std::vector<PartView> Layout::part_views() const
         pv.c0 = (int32_t)ph.c0;
         pv.xs_cols = 0;
         pv.sched = nullptr;
-        pv.pad_ = 0;
+        pv.pf_ahead = 0;
         v.push_back(pv);
     }
     return v;

@@ -9,6 +9,7 @@
 // loop kind and reused (every parameter lives in device memory).
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -48,6 +49,8 @@ struct LoopGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int kernels_per_iter = 0;
+    // host-loop mode: the iteration body, launched directly (valid during one call)
+    std::function<void(cudaStream_t, unsigned long long, int)> body;
 };
 
 // Device buffer that grows on demand.  A reallocation bumps *epoch, which
@@ -98,17 +101,24 @@ struct spg_format_t {
     DevBuf<float> partial_k;
     DevBuf<int32_t> seeds;
     DevBuf<float> X, Y;
+    DevBuf<float> aux, stage_r;
     IterState *d_state = nullptr;
     // launch views of the parts: plain (8-warp blocks) and staged (x slice in smem)
     struct Views {
         std::vector<PartView> v;
         int32_t nblk = 0;
         bool built = false;
-    } vplain, vstaged;
-    DevBuf<uint32_t> sched;      // staged-kernel counters, 2 per part (zero between launches)
+    };
+    struct LayoutRT {
+        Views vplain, vstaged;
+        DevBuf<uint32_t> sched;  // staged-kernel counters, 2 per part (zero between launches)
+    } rt_fwd, rt_bwd;
     int64_t stage_cols = kStagedMaxCols;
+    int32_t pf_ahead = 8192;     // L2 bulk-prefetch distance of the slot stream (bytes)
+    int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
     int num_sms = 152;
     std::map<std::string, LoopGraph> graphs;
+    LoopGraph host_loop;         // loop_mode 1
     uint64_t epoch = 0;          // workspace generation the cached graphs were built for
     uint64_t graphs_epoch = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -140,9 +150,10 @@ struct spg_format_t {
         cudaFree(d_rp); cudaFree(d_col); cudaFree(d_val); cudaFree(d_dangling);
         cudaFree(d_row_half); cudaFree(d_arp); cudaFree(d_acol); cudaFree(d_P);
         x.release(); y.release(); stage_in.release(); stage_out.release(); red.release();
-        sched.release();
+        rt_fwd.sched.release();
+        rt_bwd.sched.release();
         redk.release(); delta_k.release(); l1_k.release(); partial_k.release(); seeds.release();
-        X.release(); Y.release();
+        X.release(); Y.release(); aux.release(); stage_r.release();
         cudaFree(d_state);
         for (auto &kv : graphs) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -381,8 +392,11 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
             const int64_t N = h->fwd.n;
             cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
             h->stage_cols = o.x_stage_cols < 0 ? 0 : (o.x_stage_cols > 0 ? std::min<int64_t>(o.x_stage_cols, kStagedMaxCols) : kStagedMaxCols);
-            CK(h->sched.ensure(2 * h->fwd.parts.size()));
-            CK(cudaMemset(h->sched.p, 0, 2 * h->fwd.parts.size() * sizeof(uint32_t)));
+            h->pf_ahead = o.slab_prefetch < 0 ? 0 : (o.slab_prefetch > 0 ? (int32_t)std::min<int64_t>(o.slab_prefetch, 1 << 20) : 8192);
+            h->pf_ahead = (h->pf_ahead + 255) / 256 * 256;
+            h->loop_mode = o.loop_mode == 1 ? 1 : 0;
+            CK(h->rt_fwd.sched.ensure(2 * h->fwd.parts.size()));
+            CK(cudaMemset(h->rt_fwd.sched.p, 0, 2 * h->fwd.parts.size() * sizeof(uint32_t)));
             CK(cudaMalloc((void **)&h->d_state, sizeof(IterState)));
             CK(cudaEventCreate(&h->ev0));
             CK(cudaEventCreate(&h->ev1));
@@ -418,10 +432,17 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
                     ColumnSource ts;
                     ts.n = n; ts.colptr = tcp.data(); ts.rowidx = tri.data(); ts.val = tcv.data();
                     ts.eid = teid.data();
+                    // rows of M^T with no entries are the dangling nodes: they also
+                    // receive c * lambda_s in the adjoint (class bit)
+                    std::vector<uint8_t> dcls((size_t)n);
+                    for (int64_t u = 0; u < n; ++u) dcls[(size_t)u] = rp[u + 1] == rp[u] ? 1 : 0;
+                    ts.row_class = dcls.data();
                     h->bwd.reset(new Layout());
                     if (!build_layout(ts, prm, *h->bwd, err)) return fail(SPG_ERR_INVALID, err);
                     e = upload_layout(*h->bwd, o.keep_plan != 0, s);
                     if (e != cudaSuccess) return cuda_fail(e, "upload transpose");
+                    CK(h->rt_bwd.sched.ensure(2 * h->bwd->parts.size()));
+                    CK(cudaMemset(h->rt_bwd.sched.p, 0, 2 * h->bwd->parts.size() * sizeof(uint32_t)));
                 }
             }
         }
@@ -571,12 +592,12 @@ extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, in
 // shared memory, one block per SM; the rest (and every part when staging is
 // off) get 8-warp blocks, one warp per workload.  Block reduction slots are
 // laid out part after part; split rows reduce after all blocks.
-static spg_format_t::Views &get_views(spg_handle h, bool staged)
+static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
+                                        spg_format_t::LayoutRT &rt, bool staged)
 {
-    staged = staged && h->stage_cols > 0;
-    spg_format_t::Views &V = staged ? h->vstaged : h->vplain;
+    staged = staged && h->stage_cols > 0 && rt.sched.p;
+    spg_format_t::Views &V = staged ? rt.vstaged : rt.vplain;
     if (V.built) return V;
-    const Layout &L = h->fwd;
     int32_t base = 0;
     V.v.clear();
     for (size_t p = 0; p < L.parts.size(); ++p) {
@@ -586,9 +607,10 @@ static spg_format_t::Views &get_views(spg_handle h, bool staged)
         pv.wl = L.d_wl + ph.wl_off;
         pv.rows = L.d_rows;
         pv.slab = L.d_slab;
-        pv.sched = h->sched.p + 2 * p;
+        pv.sched = rt.sched.p ? rt.sched.p + 2 * p : nullptr;
         pv.nwl = (int32_t)ph.nwl_total;
         pv.c0 = (int32_t)ph.c0;
+        pv.pf_ahead = h->pf_ahead;
         const int64_t width = ph.c1 - ph.c0;
         if (staged && width >= 1024 && ph.nwl_total > 0) {
             pv.xs_cols = (int32_t)std::min<int64_t>(h->stage_cols, width);
@@ -606,15 +628,22 @@ static spg_format_t::Views &get_views(spg_handle h, bool staged)
     return V;
 }
 
-static SplitView split_of(spg_handle h, const spg_format_t::Views &V)
+static spg_format_t::Views &get_views(spg_handle h, bool staged)
 {
-    SplitView sv = h->fwd.split_view();
+    return get_views_L(h, h->fwd, h->rt_fwd, staged);
+}
+
+static SplitView split_of_L(const Layout &L, const spg_format_t::Views &V)
+{
+    SplitView sv = L.split_view();
     sv.red_split_base = V.nblk;
     return sv;
 }
 
-static int nred_of(spg_handle h, const spg_format_t::Views &V) { return V.nblk + (int)h->fwd.nsplit; }
+static SplitView split_of(spg_handle h, const spg_format_t::Views &V) { return split_of_L(h->fwd, V); }
 
+static int nred_of_L(const Layout &L, const spg_format_t::Views &V) { return V.nblk + (int)L.nsplit; }
+static int nred_of(spg_handle h, const spg_format_t::Views &V) { return nred_of_L(h->fwd, V); }
 static spg_status ensure_vectors(spg_handle h, int64_t N)
 {
     CK(h->x.ensure((size_t)N));
@@ -633,6 +662,14 @@ static spg_status device_in(spg_handle h, const float *p, int64_t count, const f
     CK(cudaMemcpyAsync(h->stage_in.p, p, count * sizeof(float), cudaMemcpyHostToDevice, s));
     *out = h->stage_in.p;
     return SPG_OK;
+}
+
+static void launch_parts_L(spg_handle h, const Layout &L, spg_format_t::LayoutRT &rt, int mode,
+                           const IterState *st, double2 *red, cudaStream_t s)
+{
+    const spg_format_t::Views &V = get_views_L(h, L, rt, true);
+    const SplitView sv = split_of_L(L, V);
+    for (const PartView &pv : V.v) launch_part(mode, pv, sv, nullptr, nullptr, st, red, s);
 }
 
 static void launch_parts(spg_handle h, int mode, const float *x, float *y, const IterState *st,
@@ -710,6 +747,12 @@ extern "C" spg_status spg_spmm(spg_handle h, const float *X, int64_t ldx, float 
 template <class Body>
 static spg_status get_loop_graph(spg_handle h, const std::string &key, Body body, LoopGraph **out)
 {
+    if (h->loop_mode == 1) {             // host loop: no graph, the body is launched per iteration
+        h->host_loop = LoopGraph();
+        h->host_loop.body = body;
+        *out = &h->host_loop;
+        return SPG_OK;
+    }
     if (h->graphs_epoch != h->epoch) {   // a workspace buffer moved: recapture
         h->drop_graphs();
         h->graphs_epoch = h->epoch;
@@ -733,7 +776,7 @@ static spg_status get_loop_graph(spg_handle h, const std::string &key, Body body
     cudaError_t e = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        body(cs, (unsigned long long)ch);
+        body(cs, (unsigned long long)ch, 1);
         cudaGraph_t captured = bodyg;
         e = cudaStreamEndCapture(cs, &captured);
     }
@@ -778,7 +821,20 @@ static spg_status run_loop(spg_handle h, LoopGraph *g, int max_iter, IterState *
 {
     if (max_iter > 0) {
         CK(cudaEventRecord(h->ev0, s));
-        CK(cudaGraphLaunch(g->exec, s));
+        if (g->exec) {
+            CK(cudaGraphLaunch(g->exec, s));
+        } else {
+            // host loop (the paper's structure): poll the done flag every 16 iterations
+            for (int it = 0; it < max_iter; ++it) {
+                g->body(s, 0ull, 0);
+                if ((it + 1) % 16 == 0 && it + 1 < max_iter) {
+                    int32_t done = 0;
+                    CK(cudaMemcpyAsync(&done, &h->d_state->done, sizeof done, cudaMemcpyDeviceToHost, s));
+                    CK(cudaStreamSynchronize(s));
+                    if (done) break;
+                }
+            }
+        }
         CK(cudaEventRecord(h->ev1, s));
     }
     CK(cudaMemcpyAsync(hs, h->d_state, sizeof(IterState), cudaMemcpyDeviceToHost, s));
@@ -819,9 +875,9 @@ extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int 
     launch_init_delta(h->d_state, s);
     LoopGraph *g;
     const int nred = nred_of(h, get_views(h, true));
-    st = get_loop_graph(h, "pagerank", [&](cudaStream_t cs, unsigned long long cond) {
+    st = get_loop_graph(h, "pagerank", [&](cudaStream_t cs, unsigned long long cond, int uc) {
         launch_parts(h, EPI_PAGERANK, nullptr, nullptr, h->d_state, h->red.p, cs);
-        launch_check(EPI_PAGERANK, h->d_state, h->red.p, nred, cond, 1, cs);
+        launch_check(EPI_PAGERANK, h->d_state, h->red.p, nred, cond, uc, cs);
     }, &g);
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
@@ -852,9 +908,9 @@ extern "C" spg_status spg_hits(spg_handle h, int norm, double tol, int max_iter,
     launch_fill(N, (float)(1.0 / (double)n), h->x.p, s);
     LoopGraph *g;
     const int nred = nred_of(h, get_views(h, true));
-    st = get_loop_graph(h, "hits", [&](cudaStream_t cs, unsigned long long cond) {
+    st = get_loop_graph(h, "hits", [&](cudaStream_t cs, unsigned long long cond, int uc) {
         launch_parts(h, EPI_HITS, nullptr, nullptr, h->d_state, h->red.p, cs);
-        launch_check(EPI_HITS, h->d_state, h->red.p, nred, cond, 1, cs);
+        launch_check(EPI_HITS, h->d_state, h->red.p, nred, cond, uc, cs);
     }, &g);
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
@@ -875,7 +931,8 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
                               void *stream)
 {
     if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
-    if (h->kind != SPG_KIND_PAGERANK) return fail(SPG_ERR_UNSUPPORTED, "rwr needs a PAGERANK handle");
+    if (h->kind != SPG_KIND_PAGERANK && !(h->kind == SPG_KIND_WEIGHTED && k == 1))
+        return fail(SPG_ERR_UNSUPPORTED, "rwr needs a PAGERANK handle (or WEIGHTED with k = 1)");
     if (!seeds || !R || k < 1 || k > 64 || !(restart > 0.f && restart <= 1.f) || max_iter < 0)
         return fail(SPG_ERR_INVALID, "bad rwr arguments (1 <= k <= 64)");
     cudaStream_t s = (cudaStream_t)stream;
@@ -901,9 +958,9 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
         CK(cudaMemsetAsync(h->x.p, 0, N * sizeof(float), s));
         launch_set_one(h->x.p, h->seeds.p, 1, s);
         launch_init_delta(h->d_state, s);
-        st = get_loop_graph(h, "rwr1", [&](cudaStream_t cs, unsigned long long cond) {
+        st = get_loop_graph(h, "rwr1", [&](cudaStream_t cs, unsigned long long cond, int uc) {
             launch_parts(h, EPI_RWR, nullptr, nullptr, h->d_state, h->red.p, cs);
-            launch_check(EPI_RWR, h->d_state, h->red.p, nred, cond, 1, cs);
+            launch_check(EPI_RWR, h->d_state, h->red.p, nred, cond, uc, cs);
         }, &g);
         if (st != SPG_OK) return st;
         CK(cudaGetLastError());
@@ -934,11 +991,11 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
     SplitView sv = split_of(h, VK);
     sv.partial = h->partial_k.p;
     const std::string key = "rwrk" + std::to_string(k);
-    st = get_loop_graph(h, key, [&](cudaStream_t cs, unsigned long long cond) {
+    st = get_loop_graph(h, key, [&](cudaStream_t cs, unsigned long long cond, int uc) {
         for (const PartView &pv : VK.v)
             launch_part_spmm(EPI_RWR, pv, sv, nullptr, nullptr, k, h->d_state, h->seeds.p,
                              h->delta_k.p, h->redk.p, cs);
-        launch_check_k(h->d_state, h->redk.p, nredk, k, h->delta_k.p, h->l1_k.p, cond, 1, cs);
+        launch_check_k(h->d_state, h->redk.p, nredk, k, h->delta_k.p, h->l1_k.p, cond, uc, cs);
     }, &g);
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
@@ -993,12 +1050,12 @@ extern "C" spg_status spg_baseline_pagerank(spg_handle h, spg_baseline which, fl
     launch_init_delta_flags(h->d_state, h->d_dangling, s);
     LoopGraph *g;
     const std::string key = which == SPG_BASELINE_CSR_SCALAR ? "pr_csr_scalar" : "pr_csr_vector";
-    st = get_loop_graph(h, key, [&](cudaStream_t cs, unsigned long long cond) {
+    st = get_loop_graph(h, key, [&](cudaStream_t cs, unsigned long long cond, int uc) {
         if (which == SPG_BASELINE_CSR_SCALAR)
             launch_csr_scalar(EPI_PAGERANK, n, h->d_rp, h->d_col, h->d_val, h->d_dangling, nullptr, nullptr, h->d_state, h->red.p, nullptr, cs);
         else
             launch_csr_vector(EPI_PAGERANK, n, h->d_rp, h->d_col, h->d_val, h->d_dangling, nullptr, nullptr, h->d_state, h->red.p, nullptr, cs);
-        launch_check(EPI_PAGERANK, h->d_state, h->red.p, nb, cond, 1, cs);
+        launch_check(EPI_PAGERANK, h->d_state, h->red.p, nb, cond, uc, cs);
     }, &g);
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
@@ -1043,24 +1100,85 @@ extern "C" spg_status spg_time_parts(spg_handle h, int mode, int reps, float *ms
 
 extern "C" spg_status spg_set_edge_logits(spg_handle h, const float *theta, void *stream)
 {
-    (void)h; (void)theta; (void)stream;
-    return fail(SPG_ERR_UNSUPPORTED, "edge logits not built yet");
+    if (!h || h->host_only || h->kind != SPG_KIND_WEIGHTED) return fail(SPG_ERR_UNSUPPORTED, "needs a WEIGHTED handle");
+    if (!theta) return fail(SPG_ERR_INVALID, "null theta");
+    cudaStream_t s = (cudaStream_t)stream;
+    const float *td = theta;
+    if (!is_device_ptr(theta)) {
+        CK(h->stage_in.ensure((size_t)h->nnz_in));
+        CK(cudaMemcpyAsync(h->stage_in.p, theta, h->nnz_in * sizeof(float), cudaMemcpyHostToDevice, s));
+        td = h->stage_in.p;
+    }
+    Layout *b = h->bwd.get();
+    launch_edge_softmax(h->n_graph, h->d_arp, td, h->fwd.d_edge_slot, h->fwd.d_slab,
+                        b ? b->d_edge_slot : nullptr, b ? b->d_slab : nullptr, h->d_P, s);
+    CK(cudaGetLastError());
+    return SPG_OK;
 }
 
 extern "C" spg_status spg_rwr_weighted(spg_handle h, float restart, int32_t seed, double tol,
                                        int max_iter, float *r, spg_iter_info *info, void *stream)
 {
-    (void)h; (void)restart; (void)seed; (void)tol; (void)max_iter; (void)r; (void)info; (void)stream;
-    return fail(SPG_ERR_UNSUPPORTED, "weighted rwr not built yet");
+    if (!h || h->kind != SPG_KIND_WEIGHTED) return fail(SPG_ERR_UNSUPPORTED, "needs a WEIGHTED handle");
+    return spg_rwr(h, restart, &seed, 1, tol, max_iter, r, info, stream);
 }
 
 extern "C" spg_status spg_rwr_adjoint(spg_handle h, float restart, int32_t seed, const float *r,
                                       const float *g, double tol, int max_iter, float *lambda,
                                       float *dtheta, spg_iter_info *info, void *stream)
 {
-    (void)h; (void)restart; (void)seed; (void)r; (void)g; (void)tol; (void)max_iter;
-    (void)lambda; (void)dtheta; (void)info; (void)stream;
-    return fail(SPG_ERR_UNSUPPORTED, "adjoint not built yet");
+    if (!h || h->host_only || h->kind != SPG_KIND_WEIGHTED) return fail(SPG_ERR_UNSUPPORTED, "needs a WEIGHTED handle");
+    if (!h->bwd) return fail(SPG_ERR_UNSUPPORTED, "adjoint needs build_transpose");
+    const int64_t n = h->n_graph;
+    if (!r || !g || seed < 0 || seed >= n || !(restart > 0.f && restart <= 1.f) || max_iter < 0)
+        return fail(SPG_ERR_INVALID, "bad adjoint arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    Layout &Lb = *h->bwd;
+    spg_status st = ensure_vectors(h, n);
+    if (st != SPG_OK) return st;
+    spg_format_t::Views &Vb = get_views_L(h, Lb, h->rt_bwd, true);
+    const int nred = nred_of_L(Lb, Vb);
+    CK(h->red.ensure((size_t)std::max(1, nred)));
+    CK(h->aux.ensure((size_t)n));
+    // g into the transposed layout's order; lambda(0) = g
+    const float *gd;
+    if ((st = device_in(h, g, n, &gd, s)) != SPG_OK) return st;
+    launch_gather(n, Lb.d_inv, gd, h->aux.p, s);
+    CK(cudaMemcpyAsync(h->x.p, h->aux.p, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    const double c = 1.0 - (double)restart;
+    IterState hs = make_state(h, c, tol, max_iter, n, h->x.p, h->y.p);
+    hs.seed = Lb.perm[(size_t)seed];
+    hs.aux = h->aux.p;
+    CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
+    LoopGraph *lg;
+    st = get_loop_graph(h, "adjoint", [&](cudaStream_t cs, unsigned long long cond, int uc) {
+        launch_parts_L(h, Lb, h->rt_bwd, EPI_ADJ, h->d_state, h->red.p, cs);
+        launch_check(EPI_PAGERANK, h->d_state, h->red.p, nred, cond, uc, cs);
+    }, &lg);
+    if (st != SPG_OK) return st;
+    CK(cudaGetLastError());
+    if ((st = run_loop(h, lg, max_iter, &hs, info, s)) != SPG_OK) return st;
+    // lambda back to original order
+    const bool lam_host = lambda && !is_device_ptr(lambda);
+    CK(h->stage_out.ensure((size_t)n));
+    float *lam_d = (lambda && !lam_host) ? lambda : h->stage_out.p;
+    launch_scatter_state(n, Lb.d_inv, h->d_state, lam_d, nullptr, 0, s);
+    if (lam_host) CK(cudaMemcpyAsync(lambda, lam_d, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (dtheta) {
+        const float *rd = r;
+        if (!is_device_ptr(r)) {
+            CK(h->stage_r.ensure((size_t)n));
+            CK(cudaMemcpyAsync(h->stage_r.p, r, n * sizeof(float), cudaMemcpyHostToDevice, s));
+            rd = h->stage_r.p;
+        }
+        const bool dt_host = !is_device_ptr(dtheta);
+        float *dt_d = dtheta;
+        if (dt_host) { CK(h->stage_in.ensure((size_t)std::max(n, h->nnz_in))); dt_d = h->stage_in.p; }
+        launch_edge_grad(n, h->d_arp, h->d_acol, h->d_P, lam_d, rd, (float)c, dt_d, s);
+        if (dt_host) CK(cudaMemcpyAsync(dtheta, dt_d, h->nnz_in * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
 }
 
 extern "C" spg_status spg_batch_pagerank(const spg_handle *graphs, int count, float damping,

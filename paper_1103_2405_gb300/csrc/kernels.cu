@@ -62,6 +62,7 @@ struct Epi {
     int64_t dstart;
     float sc[2];
     int hnorm;
+    const float *aux;
 };
 
 template <int MODE>
@@ -69,8 +70,12 @@ __device__ __forceinline__ Epi load_epi(const IterState *st)
 {
     Epi E;
     E.c = 1.f; E.base = 0.f; E.tele = 0.f; E.seed = -1; E.dstart = 0;
-    E.sc[0] = E.sc[1] = 1.f; E.hnorm = 2;
-    if (MODE == EPI_PAGERANK || MODE == EPI_RWR) {
+    E.sc[0] = E.sc[1] = 1.f; E.hnorm = 2; E.aux = nullptr;
+    if (MODE == EPI_ADJ) {
+        E.c = (float)st->c;
+        E.seed = st->seed;
+        E.aux = st->aux;
+    } else if (MODE == EPI_PAGERANK || MODE == EPI_RWR) {
         const double c = st->c, d = st->delta;
         E.c = (float)c;
         E.dstart = st->dangling_start;
@@ -101,6 +106,13 @@ __device__ __forceinline__ void epilogue(const Epi &E, uint32_t rid, float tot,
         y[v] = f;
         r0 += fabs((double)f - (double)x[v]);
         if ((int64_t)v >= E.dstart) r1 += (double)f;
+    } else if (MODE == EPI_ADJ) {
+        // lambda = c K^T lambda + g with K^T = M^T + 1_D e_s^T: dangling rows
+        // (class bit) also receive c * lambda_s
+        const float add = (rid & kRowClass) ? E.c * x[E.seed] : 0.f;
+        const float f = fmaf(E.c, tot, add + __ldg(E.aux + v));
+        y[v] = f;
+        r0 += fabs((double)f - (double)x[v]);
     } else {  // HITS: a-rows read the hub half and vice versa
         const int cls = (rid & kRowClass) ? 1 : 0;
         float f = tot * (cls ? E.sc[0] : E.sc[1]);
@@ -186,6 +198,28 @@ __device__ __forceinline__ float slot_fma_g(uint2 v, const G &g, float acc)
     return fmaf(__uint_as_float(v.y), xv, acc);
 }
 
+// Bulk prefetch of a workload's slots into L2 (TMA, fire and forget): a
+// workload's slab region is consumed front to back, so lane 0 keeps the
+// prefetched frontier `ahead` bytes in front of the consumed position.  The
+// region starts on a 256-byte boundary and spans a multiple of 256 bytes.
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+struct SlabPrefetch {
+    const char *base;
+    unsigned total, done, ahead;
+    __device__ __forceinline__ void advance(unsigned consumed, int lane)
+    {
+        while (done < total && done < consumed + ahead) {
+            const unsigned n = min(4096u, total - done);
+            if (lane == 0) l2_prefetch(base + done, n);
+            done += n;
+        }
+    }
+};
+
 // One workload (Solution 3) computed by the calling warp.
 template <int MODE, class G>
 __device__ __forceinline__ void do_workload(const Workload &d, const PartView &pv,
@@ -195,42 +229,56 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
 {
     const uint32_t *__restrict__ rows = pv.rows + d.rows;
     const uint2 *__restrict__ slab = pv.slab + d.slab;
+    const int hp = d.major == 0 ? d.h : (d.h + 31) & ~31;
+    SlabPrefetch pf{reinterpret_cast<const char *>(slab), (unsigned)((int64_t)hp * d.w * 8), 0u,
+                    (unsigned)pv.pf_ahead};
+    if (pf.ahead) pf.advance(0u, lane);
     if (d.major == 0) {
-        // row-major (CSR-vector): the warp strides across one row at a time
+        // row-major (CSR-vector): the warp strides across one row at a time,
+        // 8 slots per lane in flight before their gathers
         for (int i = 0; i < d.h; ++i) {
             const uint2 *s = slab + (int64_t)i * d.w;
             float acc = 0.f;
             int e = lane;
-            for (; e + 96 < d.w; e += 128) {
-                const uint2 a0 = __ldcs(s + e), a1 = __ldcs(s + e + 32);
-                const uint2 a2 = __ldcs(s + e + 64), a3 = __ldcs(s + e + 96);
-                acc = slot_fma_g(a0, g, acc);
-                acc = slot_fma_g(a1, g, acc);
-                acc = slot_fma_g(a2, g, acc);
-                acc = slot_fma_g(a3, g, acc);
+            for (; e + 224 < d.w; e += 256) {
+                if (pf.ahead) pf.advance((unsigned)(((int64_t)i * d.w + e - lane) * 8), lane);
+                uint2 a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = __ldcs(s + e + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc = slot_fma_g(a[u], g, acc);
+            }
+            if (e + 96 < d.w) {
+                uint2 a[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = __ldcs(s + e + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc = slot_fma_g(a[u], g, acc);
+                e += 128;
             }
             for (; e < d.w; e += 32) acc = slot_fma_g(__ldcs(s + e), g, acc);
             acc = warp_sum(acc);
             if (lane == 0) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc, x, y, r0, r1);
+            if (pf.ahead) pf.advance((unsigned)((int64_t)(i + 1) * d.w * 8), lane);
         }
     } else {
         // column-major (ELL): one row per lane, 32-row blocks
-        const int hp = (d.h + 31) & ~31;
         for (int b = 0; b < hp; b += 32) {
             const uint2 *s = slab + (int64_t)b * d.w + lane;
             float acc = 0.f;
             int e = 0;
-            for (; e + 3 < d.w; e += 4) {
-                const uint2 a0 = __ldcs(s + (int64_t)e * 32), a1 = __ldcs(s + (int64_t)(e + 1) * 32);
-                const uint2 a2 = __ldcs(s + (int64_t)(e + 2) * 32), a3 = __ldcs(s + (int64_t)(e + 3) * 32);
-                acc = slot_fma_g(a0, g, acc);
-                acc = slot_fma_g(a1, g, acc);
-                acc = slot_fma_g(a2, g, acc);
-                acc = slot_fma_g(a3, g, acc);
+            for (; e + 7 < d.w; e += 8) {
+                if (pf.ahead) pf.advance((unsigned)(((int64_t)b * d.w + (int64_t)e * 32) * 8), lane);
+                uint2 a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = __ldcs(s + (int64_t)(e + u) * 32);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc = slot_fma_g(a[u], g, acc);
             }
             for (; e < d.w; ++e) acc = slot_fma_g(__ldcs(s + (int64_t)e * 32), g, acc);
             const int i = b + lane;
             if (i < d.h) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc, x, y, r0, r1);
+            if (pf.ahead) pf.advance((unsigned)((int64_t)(b + 32) * d.w * 8), lane);
         }
     }
 }
@@ -343,6 +391,7 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
         case EPI_RAW: launch_staged<EPI_RAW>(pv, sv, x, y, st, red, s); break;
         case EPI_PAGERANK: launch_staged<EPI_PAGERANK>(pv, sv, x, y, st, red, s); break;
         case EPI_RWR: launch_staged<EPI_RWR>(pv, sv, x, y, st, red, s); break;
+        case EPI_ADJ: launch_staged<EPI_ADJ>(pv, sv, x, y, st, red, s); break;
         default: launch_staged<EPI_HITS>(pv, sv, x, y, st, red, s); break;
         }
         count_launches(1);
@@ -353,6 +402,7 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
     case EPI_RAW: k_part<EPI_RAW><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     case EPI_PAGERANK: k_part<EPI_PAGERANK><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     case EPI_RWR: k_part<EPI_RWR><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
+    case EPI_ADJ: k_part<EPI_ADJ><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     default: k_part<EPI_HITS><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     }
     count_launches(1);
@@ -590,6 +640,7 @@ __global__ void __launch_bounds__(1024)
 k_check(int mode, IterState *st, const double2 *__restrict__ red, int nred,
         cudaGraphConditionalHandle cond, int use_cond)
 {
+    if (st->done) return;   // host-loop mode may launch past convergence
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < nred; i += blockDim.x) {
         const double2 v = red[i];
@@ -632,6 +683,7 @@ k_check_k(IterState *st, const double *__restrict__ redk, int nred, int k, doubl
 {
     __shared__ double part_sum[1024];
     __shared__ double colmax[64];
+    if (st->done) return;   // host-loop mode may launch past convergence
     const int Q = 2 * k;
     const int P = blockDim.x / Q;
     const int q = threadIdx.x % Q, p = threadIdx.x / Q;

@@ -11,7 +11,8 @@ enum EpiMode {
     EPI_RAW = 0,       // y' = (M' x')_v
     EPI_PAGERANK = 1,  // y' = c (M' x')_v + (c delta + 1 - c)/n;  sum |y'-x'|, dangling sum
     EPI_RWR = 2,       // y' = c (M' x')_v + [v == s](c delta + 1 - c); same sums
-    EPI_HITS = 3       // y' = (M' x')_v * scale[other half];  per-half sum or sum of squares
+    EPI_HITS = 3,      // y' = (M' x')_v * scale[other half];  per-half sum or sum of squares
+    EPI_ADJ = 4        // y' = c (M'^T x')_v + [v dangling] c x'_s + g'_v;  sum |y'-x'|
 };
 
 // One tiled-composite launch of one part (Solution 3: one warp per

@@ -59,7 +59,7 @@ struct PartView {
     int32_t red_base;     // first reduction slot of this part's blocks
     int32_t c0;           // first column of the part
     int32_t xs_cols;      // > 0: columns [c0, c0 + xs_cols) staged in shared memory
-    int32_t pad_;
+    int32_t pf_ahead;     // bytes of a workload's slots prefetched into L2 ahead of use (0 = off)
 };
 
 // Largest x slice staged in shared memory (floats): 192 KB.
@@ -92,6 +92,7 @@ struct IterState {
     int64_t n;
     int64_t dangling_start;
     float *buf[2];        // ping-pong iterates (permuted order)
+    const float *aux;     // adjoint: the loss gradient g in permuted order
 };
 
 }  // namespace spg
