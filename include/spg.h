@@ -66,7 +66,9 @@ typedef enum {
     /* The CSR is A and `val` holds per-edge logits theta (A's CSR order).
      * M(v,u) = softmax over u's out-edges of theta; rwr_weighted and
      * rwr_adjoint use it, and spg_set_edge_logits rewrites it in place. */
-    SPG_KIND_WEIGHTED = 3
+    SPG_KIND_WEIGHTED = 3,
+    /* A batch of independent graphs (spg_build_batch only). */
+    SPG_KIND_BATCH = 4
 } spg_kind;
 
 /* Compressed sparse rows: n_rows + 1 row offsets (int64), nnz column indices
@@ -123,14 +125,21 @@ typedef struct {
      * 0 = auto (49152, i.e. 192 KB), < 0 = off (x gathered through L1/L2). */
     int64_t x_stage_cols;
     /* Distance, in bytes, by which each warp's bulk L2 prefetch of its slots
-     * runs ahead of their use (TMA cp.async.bulk.prefetch).  0 = auto (8 KB),
-     * < 0 = off. */
+     * runs ahead of their use (TMA cp.async.bulk.prefetch).  <= 0 = off (the
+     * default: measured slower at R-MAT scale 22, the slot stream is not the
+     * latency that limits the kernel). */
     int64_t slab_prefetch;
     /* 0 = power iterations inside one CUDA graph with a conditional WHILE
      * node (default); 1 = a host loop of direct launches that polls the
      * convergence flag every 16 iterations (the paper's structure; also what
      * a kernel profiler can attribute launch by launch). */
     int loop_mode;
+    /* Most rows one workload may hold (not in the paper; GB300): a warp
+     * walks its workload's 32-row blocks in sequence, so a tall workload of
+     * one-entry rows is a long serial chain of dependent loads.  The
+     * Algorithm 3 model sees the capped rectangles.  0 = auto (256),
+     * < 0 = no cap (the paper's packing). */
+    int64_t max_rows;
 } spg_build_opts;
 
 /* Per-call results of the power iterations. */
@@ -286,15 +295,31 @@ spg_status spg_rwr_adjoint(spg_handle h, float restart, int32_t seed, const floa
 
 /* ------------------------------------------------------ batched graphs -- */
 
-/* PageRank on `count` independent PAGERANK handles at once, in ONE persistent
- * launch per iteration sweep, the whole solve captured in a CUDA graph (not
- * in the paper; batching of small graphs).  Graphs are scheduled longest
- * first over the SMs; each graph runs its own tolerance test.  p_out[g] is
- * graph g's n_g FP32 output (device pointers); info (nullable) gets one
- * entry per graph. */
-spg_status spg_batch_pagerank(const spg_handle *graphs, int count, float damping, double tol,
-                              int max_iter, float *const *p_out, spg_iter_info *info,
-                              void *stream);
+/* Build one handle over `count` independent graphs (adjacency CSRs, as for
+ * SPG_KIND_PAGERANK; host or device pointers per csr).  The graphs become the
+ * diagonal blocks of one matrix; the degree order of Section 3.1 Solution 2
+ * is taken within each graph, the composite partition (Solution 3) over all
+ * of them, so one launch sweeps every graph (not in the paper; batching of
+ * many small graphs).  opts->tile_width is ignored (one part).  Graph g's
+ * nodes occupy positions [offsets[g], offsets[g+1]) of the concatenated
+ * vectors (spg_batch_offsets). */
+spg_status spg_build_batch(const spg_csr *graphs, int count, const spg_build_opts *opts,
+                           void *stream, spg_handle *out);
+
+/* count + 1 node offsets of a batch handle (host int64 array). */
+spg_status spg_batch_offsets(spg_handle h, int64_t *offsets);
+
+/* PageRank (Eq. 6, uniform dangling redistribution per graph) on every graph
+ * of a batch handle at once: per iteration one tiled-composite launch over
+ * all graphs, one block per graph for its L1 change and dangling mass, one
+ * check block; the whole solve is one CUDA graph with a WHILE node.  Each
+ * graph records the iteration at which its L1 change first went below tol;
+ * the loop ends when all have (or at max_iter).  p_out: the concatenated
+ * vectors, original node order within each graph.  info (nullable): count
+ * entries, one per graph (iters = its convergence iteration, last_l1 = its
+ * final L1 change, dangling = its final dangling mass). */
+spg_status spg_batch_pagerank(spg_handle h, float damping, double tol, int max_iter,
+                              float *p_out, spg_iter_info *info, void *stream);
 
 /* ------------------------------------------------------------ baselines -- */
 

@@ -59,11 +59,11 @@ def _load():
                 "orc_rwr_adjoint": ([i64, P, P, P, i64, dbl, P, P, dbl, i32, P, P], i32),
                 "orc_degree_order": ([i64, P, P, P], None),
                 "orc_alg1_tiles": ([i64, P, i64], i64),
-                "orc_alg3_model": ([i64, P, i64, i64, i32, i32, P], dbl),
-                "orc_alg2_partition": ([i64, P, i64, i64, i32, i32, P, P], i64),
+                "orc_alg3_model": ([i64, P, i64, i64, i32, i32, P, i64], dbl),
+                "orc_alg2_partition": ([i64, P, i64, i64, i32, i32, P, P, i64], i64),
                 "orc_partition_tile": ([i64, P, P, i64, i64, i64, i32, i32, P, P, P, P, P, P,
-                                        P, P, P, P], i64),
-                "orc_tune_heavy": ([i64, P, P, i64, i32, i32, P, dbl, P], i64),
+                                        P, P, P, P, i64], i64),
+                "orc_tune_heavy": ([i64, P, P, i64, i32, i32, P, dbl, P, i64], i64),
                 "orc_bitonic_partition": ([i64, P, i32, P], None),
             }
             for name, (args, res) in sig.items():
@@ -234,23 +234,24 @@ def alg1_tiles(sorted_col_len, tile_width):
     return int(_load().orc_alg1_tiles(s.shape[0], _p(s), int(tile_width)))
 
 
-def alg3_model(row_len, WL, max_warps, rule, table):
+def alg3_model(row_len, WL, max_warps, rule, table, max_rows=0):
     nlog, perf = table
     rl = _c(row_len, np.int64)
     return float(_load().orc_alg3_model(rl.shape[0], _p(rl), int(WL), int(max_warps), int(rule),
-                                        int(nlog), _p(_c(perf, np.float64))))
+                                        int(nlog), _p(_c(perf, np.float64)), int(max_rows)))
 
 
-def alg2_partition(row_len, nnz, max_warps, rule, table):
+def alg2_partition(row_len, nnz, max_warps, rule, table, max_rows=0):
     nlog, perf = table
     rl = _c(row_len, np.int64)
     t = ctypes.c_double(0)
     wl = _load().orc_alg2_partition(rl.shape[0], _p(rl), int(nnz), int(max_warps), int(rule),
-                                    int(nlog), _p(_c(perf, np.float64)), ctypes.byref(t))
+                                    int(nlog), _p(_c(perf, np.float64)), ctypes.byref(t),
+                                    int(max_rows))
     return int(wl), float(t.value)
 
 
-def partition_tile(row_id, row_len, heavy, wl, max_warps, rule, table):
+def partition_tile(row_id, row_len, heavy, wl, max_warps, rule, table, max_rows=0):
     """Composite partition of one tile (Solution 3 + Algorithms 2-3).
 
     Returns dict(WL, rank_row, rank_chunk, rank_len, wl_first, wl_h, wl_w, wl_major)."""
@@ -266,26 +267,27 @@ def partition_tile(row_id, row_len, heavy, wl, max_warps, rule, table):
     WL = _load().orc_partition_tile(row_id.shape[0], _p(row_id), _p(row_len), int(heavy), int(wl),
                                     int(max_warps), int(rule), int(nlog),
                                     _p(_c(perf, np.float64)), ctypes.byref(nv), _p(rr), _p(rc),
-                                    _p(rl), ctypes.byref(nw), _p(f), _p(h), _p(w), _p(mj))
+                                    _p(rl), ctypes.byref(nw), _p(f), _p(h), _p(w), _p(mj),
+                                    int(max_rows))
     k, j = nv.value, nw.value
     return dict(WL=int(WL), rank_row=rr[:k].copy(), rank_chunk=rc[:k].copy(),
                 rank_len=rl[:k].copy(), wl_first=f[:j].copy(), wl_h=h[:j].copy(),
                 wl_w=w[:j].copy(), wl_major=mj[:j].copy())
 
 
-def tune_heavy(row_id, row_len, max_warps, rule, table, split_cost):
+def tune_heavy(row_id, row_len, max_warps, rule, table, split_cost, max_rows=0):
     nlog, perf = table
     row_id = _c(row_id, np.int64)
     row_len = _c(row_len, np.int64)
     wl = ctypes.c_int64(0)
     H = _load().orc_tune_heavy(row_id.shape[0], _p(row_id), _p(row_len), int(max_warps),
                                int(rule), int(nlog), _p(_c(perf, np.float64)), float(split_cost),
-                               ctypes.byref(wl))
+                               ctypes.byref(wl), int(max_rows))
     return int(H), int(wl.value)
 
 
 def plan_format(a_rowptr, a_col, tile_width, max_warps, table, heavy=-1, wl=0, rule=1,
-                split_cost=0.0, M=None):
+                split_cost=0.0, M=None, max_rows=0):
     """The tiled composite layout of M = W^T, step by step in the paper's order.
 
     1. column lengths of M (= out-degrees), symmetric order by decreasing
@@ -318,10 +320,10 @@ def plan_format(a_rowptr, a_col, tile_width, max_warps, table, heavy=-1, wl=0, r
         touched |= rl > 0
         ids = np.arange(n, dtype=np.int64)
         if heavy < 0:
-            H, _ = tune_heavy(ids, rl, max_warps, rule, table, split_cost)
+            H, _ = tune_heavy(ids, rl, max_warps, rule, table, split_cost, max_rows)
         else:
             H = heavy
-        part = partition_tile(ids, rl, H, wl, max_warps, rule, table)
+        part = partition_tile(ids, rl, H, wl, max_warps, rule, table, max_rows)
         tiles.append((c0, c1, H, part))
     zero_rows = np.flatnonzero(~touched).astype(np.int64)
     return dict(pi=pi, inv=inv, ntile=ntile, tiles=tiles, zero_rows=zero_rows)

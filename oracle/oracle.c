@@ -396,19 +396,29 @@ static int pick_major(int rule, int64_t w, int64_t h)
  * Readings: a workload starting at rank i takes h = max(1, floor(WL / w))
  * rows, w = length of row i, clipped at the rows left; Size and the table
  * lookup use the padded rectangle; the iteration count is that of the warps
- * actually formed.
+ * actually formed.  [GB300 reading] with max_rows > 0 a workload also holds
+ * at most max_rows rows (a warp walks its rows' 32-row blocks one after
+ * another, so a tall workload of one-entry rows is a long serial chain).
  */
+static int64_t wl_rows(int64_t WL, int64_t w, int64_t left, int64_t max_rows)
+{
+    int64_t h = WL / w;
+    if (h < 1) h = 1;
+    if (max_rows > 0 && h > max_rows) h = max_rows;
+    if (h > left) h = left;
+    return h;
+}
+
 double orc_alg3_model(int64_t nrows, const int64_t *row_len, int64_t WL,
-                      int64_t max_warps, int rule, int nlog, const double *perf)
+                      int64_t max_warps, int rule, int nlog, const double *perf,
+                      int64_t max_rows)
 {
     orc_table t = { nlog, perf };
     if (nrows <= 0) return 0.0;
     int64_t nwarp = 0;
     for (int64_t i = 0; i < nrows; ) {
-        int64_t w = row_len[i], h = w > 0 ? WL / w : nrows - i;
-        if (h < 1) h = 1;
-        if (h > nrows - i) h = nrows - i;
-        i += h; ++nwarp;
+        i += wl_rows(WL, row_len[i], nrows - i, max_rows);
+        ++nwarp;
     }
     int64_t iters = (nwarp + max_warps - 1) / max_warps;
     double *P = (double *)calloc((size_t)iters, sizeof(double));
@@ -416,9 +426,7 @@ double orc_alg3_model(int64_t nrows, const int64_t *row_len, int64_t WL,
     int64_t *cnt = (int64_t *)calloc((size_t)iters, sizeof(int64_t));
     int64_t j = 0;
     for (int64_t i = 0; i < nrows; ++j) {
-        int64_t w = row_len[i], h = w > 0 ? WL / w : nrows - i;
-        if (h < 1) h = 1;
-        if (h > nrows - i) h = nrows - i;
+        int64_t w = row_len[i], h = wl_rows(WL, w, nrows - i, max_rows);
         int major = pick_major(rule, w, h);
         int64_t wp = major == 0 ? round_up32(w) : w;
         int64_t hp = major == 0 ? h : round_up32(h);
@@ -443,19 +451,19 @@ double orc_alg3_model(int64_t nrows, const int64_t *row_len, int64_t WL,
  * row.  Returns WL; *best_time gets its modelled time. */
 int64_t orc_alg2_partition(int64_t nrows, const int64_t *row_len, int64_t nnz,
                            int64_t max_warps, int rule, int nlog,
-                           const double *perf, double *best_time)
+                           const double *perf, double *best_time, int64_t max_rows)
 {
     if (nrows <= 0) { if (best_time) *best_time = 0.0; return 0; }
     int64_t low = row_len[0];
     int64_t opt = 0;
     double opt_t = INFINITY;
     for (int64_t WL = low; WL * max_warps <= nnz; WL += low) {
-        double t = orc_alg3_model(nrows, row_len, WL, max_warps, rule, nlog, perf);
+        double t = orc_alg3_model(nrows, row_len, WL, max_warps, rule, nlog, perf, max_rows);
         if (t < opt_t) { opt_t = t; opt = WL; }
     }
     if (opt == 0) {
         opt = low;
-        opt_t = orc_alg3_model(nrows, row_len, low, max_warps, rule, nlog, perf);
+        opt_t = orc_alg3_model(nrows, row_len, low, max_warps, rule, nlog, perf, max_rows);
     }
     if (best_time) *best_time = opt_t;
     return opt;
@@ -470,7 +478,8 @@ int64_t orc_alg2_partition(int64_t nrows, const int64_t *row_len, int64_t nnz,
  *      virtual rows (ties: row id, then chunk index); heavy <= 0 disables it;
  *   3. WL = wl if wl > 0, else Algorithm 2 over the virtual row lengths;
  *   4. pack: a workload starting at rank i has w = length of row i and
- *      h = max(1, floor(WL / w)) rows (clipped), stored by pick_major().
+ *      h = max(1, floor(WL / w)) rows (clipped at the rows left and, when
+ *      max_rows > 0, at max_rows), stored by pick_major().
  * Rows of length 0 are not part of any workload.
  * Outputs: rank_row[k], rank_chunk[k], rank_len[k] for k < *nvirt, and per
  * workload wl_first[j] (rank of its first row), wl_h[j], wl_w[j],
@@ -495,7 +504,7 @@ int64_t orc_partition_tile(int64_t nrows, const int64_t *row_id,
                            int64_t *rank_row, int64_t *rank_chunk,
                            int64_t *rank_len, int64_t *nwl_out,
                            int64_t *wl_first, int64_t *wl_h, int64_t *wl_w,
-                           int64_t *wl_major)
+                           int64_t *wl_major, int64_t max_rows)
 {
     int64_t nv = 0, nnz = 0;
     for (int64_t r = 0; r < nrows; ++r) {
@@ -532,12 +541,10 @@ int64_t orc_partition_tile(int64_t nrows, const int64_t *row_id,
     }
     *nvirt_out = nv;
     int64_t WL = wl > 0 ? wl
-        : orc_alg2_partition(nv, rank_len, nnz, max_warps, rule, nlog, perf, NULL);
+        : orc_alg2_partition(nv, rank_len, nnz, max_warps, rule, nlog, perf, NULL, max_rows);
     int64_t j = 0;
     for (int64_t i = 0; i < nv; ++j) {
-        int64_t w = rank_len[i], h = WL / w;
-        if (h < 1) h = 1;
-        if (h > nv - i) h = nv - i;
+        int64_t w = rank_len[i], h = wl_rows(WL, w, nv - i, max_rows);
         wl_first[j] = i; wl_h[j] = h; wl_w[j] = w;
         wl_major[j] = pick_major(rule, w, h);
         i += h;
@@ -588,7 +595,7 @@ double orc_split_cost_chunks(int64_t nrows, const int64_t *row_len, int64_t H)
 int64_t orc_tune_heavy(int64_t nrows, const int64_t *row_id,
                        const int64_t *row_len, int64_t max_warps, int rule,
                        int nlog, const double *perf, double split_cost,
-                       int64_t *wl_out)
+                       int64_t *wl_out, int64_t max_rows)
 {
     int64_t nnz = 0, nv_cap = 0;
     for (int64_t r = 0; r < nrows; ++r)
@@ -615,8 +622,8 @@ int64_t orc_tune_heavy(int64_t nrows, const int64_t *row_id,
         int64_t nv = 0, nwl = 0;
         int64_t WL = orc_partition_tile(nrows, row_id, row_len, H, 0, max_warps,
                                         rule, nlog, perf, &nv, rr, rc, rl, &nwl,
-                                        f, hh, ww, mm);
-        double t = orc_alg3_model(nv, rl, WL, max_warps, rule, nlog, perf) +
+                                        f, hh, ww, mm, max_rows);
+        double t = orc_alg3_model(nv, rl, WL, max_warps, rule, nlog, perf, max_rows) +
                    split_cost * orc_split_cost_chunks(nrows, row_len, H);
         if (t < best) { best = t; bestH = H; bestWL = WL; }
     }

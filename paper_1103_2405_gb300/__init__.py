@@ -43,7 +43,8 @@ class _Opts(ctypes.Structure):
                 ("build_transpose", ctypes.c_int), ("keep_plan", ctypes.c_int),
                 ("keep_csr", ctypes.c_int), ("device", ctypes.c_int), ("split_cost", ctypes.c_double),
                 ("tune_table_path", ctypes.c_char_p), ("x_stage_cols", ctypes.c_int64),
-                ("slab_prefetch", ctypes.c_int64), ("loop_mode", ctypes.c_int)]
+                ("slab_prefetch", ctypes.c_int64), ("loop_mode", ctypes.c_int),
+                ("max_rows", ctypes.c_int64)]
 
 
 class IterInfo(ctypes.Structure):
@@ -71,7 +72,8 @@ class _TileInfo(ctypes.Structure):
 EXPORTS = ["spg_build_format", "spg_destroy", "spg_format_info", "spg_tile_info", "spg_format_perm",
            "spg_format_export_plan", "spg_format_export_entries", "spg_format_zero_rows",
            "spg_spmv", "spg_spmv_permuted", "spg_spmm", "spg_pagerank", "spg_rwr", "spg_hits",
-           "spg_set_edge_logits", "spg_rwr_weighted", "spg_rwr_adjoint", "spg_batch_pagerank",
+           "spg_set_edge_logits", "spg_rwr_weighted", "spg_rwr_adjoint", "spg_build_batch",
+           "spg_batch_offsets", "spg_batch_pagerank",
            "spg_baseline_spmv", "spg_baseline_pagerank", "spg_time_parts", "spg_load_table", "spg_launch_count",
            "spg_status_string", "spg_last_error", "spg_version"]
 
@@ -105,7 +107,9 @@ def lib():
             "spg_set_edge_logits": [P, P, P],
             "spg_rwr_weighted": [P, f32, i32, f64, i32, P, ctypes.POINTER(IterInfo), P],
             "spg_rwr_adjoint": [P, f32, i32, P, P, f64, i32, P, P, ctypes.POINTER(IterInfo), P],
-            "spg_batch_pagerank": [P, i32, f32, f64, i32, P, ctypes.POINTER(IterInfo), P],
+            "spg_build_batch": [P, i32, ctypes.POINTER(_Opts), P, ctypes.POINTER(P)],
+            "spg_batch_offsets": [P, P],
+            "spg_batch_pagerank": [P, f32, f64, i32, P, P, P],
             "spg_baseline_spmv": [P, i32, P, P, f32, f32, P],
             "spg_baseline_pagerank": [P, i32, f32, f64, i32, P, ctypes.POINTER(IterInfo), P],
             "spg_time_parts": [P, i32, i32, P, P],
@@ -192,7 +196,7 @@ class Format:
     def __init__(self, rowptr, col, val=None, kind="pagerank", tile_width=0, wl=0, heavy_row=-1,
                  layout_rule=1, max_warps=0, vec_width=1, build_transpose=False, keep_plan=False,
                  keep_csr=False, host_only=False, split_cost=0.0, table=None, x_stage_cols=0,
-                 slab_prefetch=0, loop_mode=0, stream=None):
+                 slab_prefetch=0, loop_mode=0, max_rows=0, stream=None):
         L = lib()
         self._h = ctypes.c_void_p(None)
         on_dev = _is_torch(rowptr) and rowptr.is_cuda
@@ -212,7 +216,7 @@ class Format:
                      int(vec_width), int(bool(build_transpose)), int(bool(keep_plan)),
                      int(bool(keep_csr)), -1 if host_only else 0, float(split_cost),
                      None if tpath is None else str(tpath).encode(), int(x_stage_cols),
-                     int(slab_prefetch), int(loop_mode))
+                     int(slab_prefetch), int(loop_mode), int(max_rows))
         _check(L.spg_build_format(ctypes.byref(csr), KIND[kind], ctypes.byref(opts),
                                   _stream(stream), ctypes.byref(self._h)))
         self.kind = kind
@@ -405,6 +409,64 @@ def _autograd():
             return dth, None, None, None, None, None
 
     return RWRStationary
+
+
+class BatchFormat:
+    """Many independent graphs in one handle (spg_build_batch): one
+    tiled-composite sweep per iteration over all of them."""
+
+    def __init__(self, graphs, heavy_row=-1, layout_rule=1, max_warps=0, x_stage_cols=0,
+                 slab_prefetch=0, loop_mode=0, max_rows=0, host_only=False, table=None,
+                 stream=None):
+        L = lib()
+        keep = []
+        arr = (_Csr * len(graphs))()
+        for g, (rp, col) in enumerate(graphs):
+            rp = np.ascontiguousarray(rp, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            keep += [rp, col]
+            n = rp.shape[0] - 1
+            arr[g] = _Csr(n, n, int(col.shape[0]), ctypes.c_void_p(rp.ctypes.data),
+                          ctypes.c_void_p(col.ctypes.data), None, 0)
+        tpath = table if table is not None else (TABLE_PATH if os.path.exists(TABLE_PATH) else None)
+        opts = _Opts(0, 0, int(heavy_row), int(layout_rule), int(max_warps), 1, 0, 0, 0,
+                     -1 if host_only else 0, 0.0, None if tpath is None else str(tpath).encode(),
+                     int(x_stage_cols), int(slab_prefetch), int(loop_mode), int(max_rows))
+        self._h = ctypes.c_void_p(None)
+        _check(L.spg_build_batch(ctypes.cast(arr, ctypes.c_void_p), len(graphs), ctypes.byref(opts),
+                                 _stream(stream), ctypes.byref(self._h)))
+        self.count = len(graphs)
+        self.offsets = np.empty(self.count + 1, np.int64)
+        _check(L.spg_batch_offsets(self._h, _ptr(self.offsets)[0]))
+        self.n = int(self.offsets[-1])
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().spg_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        i = _Info()
+        _check(lib().spg_format_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in _Info._fields_}
+
+    def pagerank(self, damping=0.85, tol=1e-8, max_iter=1000, out=None, like=None, stream=None):
+        """Concatenated PageRank vectors and one info dict per graph."""
+        out = _empty_like_vec(like if like is not None else np.empty(0), self.n) if out is None else out
+        infos = (IterInfo * self.count)()
+        _check(lib().spg_batch_pagerank(self._h, float(damping), float(tol), int(max_iter),
+                                        _ptr(out)[0], ctypes.cast(infos, ctypes.c_void_p),
+                                        _stream(stream)), allow_not_converged=True)
+        return out, [x.as_dict() for x in infos]
+
+    def split(self, vec):
+        return [vec[self.offsets[g]:self.offsets[g + 1]] for g in range(self.count)]
 
 
 _rwr_fn = None

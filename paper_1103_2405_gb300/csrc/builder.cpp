@@ -134,10 +134,15 @@ static inline int pick_major(int rule, int64_t w, int64_t h)
     return h * ru32(w) <= ru32(h) * w ? 0 : 1;            // fewer padded slots
 }
 
-static inline int64_t wl_height(int64_t WL, int64_t w, int64_t left)
+// Rows of a workload starting at a row of length w: floor(WL / w), at least
+// one, at most max_rows (GB300: a warp walks its 32-row blocks in sequence,
+// so a tall workload of one-entry rows is a long serial chain) and at most
+// the rows left.
+static inline int64_t wl_height(int64_t WL, int64_t w, int64_t left, int64_t max_rows)
 {
     int64_t h = WL / w;
     if (h < 1) h = 1;
+    if (max_rows > 0 && h > max_rows) h = max_rows;
     if (h > left) h = left;
     return h;
 }
@@ -147,13 +152,13 @@ static inline int64_t wl_height(int64_t WL, int64_t w, int64_t left)
 // mean table performance of its warps (Eqs. 3-5); the total is the sum
 // (Eq. 2).
 double model_time(const int32_t *vlen, int64_t nv, int64_t WL, int64_t max_warps, int rule,
-                  const PerfTable &t)
+                  int64_t max_rows, const PerfTable &t)
 {
     if (nv <= 0) return 0.0;
     double total = 0.0, P = 0.0, S = 0.0;
     int64_t cnt = 0, j = 0;
     for (int64_t i = 0; i < nv; ++j) {
-        int64_t w = vlen[i], h = wl_height(WL, w, nv - i);
+        int64_t w = vlen[i], h = wl_height(WL, w, nv - i, max_rows);
         int major = pick_major(rule, w, h);
         int64_t wp = major == 0 ? ru32(w) : w, hp = major == 0 ? h : ru32(h);
         if (j > 0 && j % max_warps == 0) {
@@ -174,18 +179,18 @@ double model_time(const int32_t *vlen, int64_t nv, int64_t WL, int64_t max_warps
 // WL <= nnz / max_warps; the first minimum wins; an empty range gives the
 // longest row.
 int64_t alg2_search(const int32_t *vlen, int64_t nv, int64_t nnz, int64_t max_warps, int rule,
-                    const PerfTable &t, double *best)
+                    int64_t max_rows, const PerfTable &t, double *best)
 {
     if (nv <= 0) { if (best) *best = 0.0; return 0; }
     int64_t low = vlen[0], opt = 0;
     double opt_t = std::numeric_limits<double>::infinity();
     for (int64_t WL = low; WL * max_warps <= nnz; WL += low) {
-        double tt = model_time(vlen, nv, WL, max_warps, rule, t);
+        double tt = model_time(vlen, nv, WL, max_warps, rule, max_rows, t);
         if (tt < opt_t) { opt_t = tt; opt = WL; }
     }
     if (opt == 0) {
         opt = low;
-        opt_t = model_time(vlen, nv, low, max_warps, rule, t);
+        opt_t = model_time(vlen, nv, low, max_warps, rule, max_rows, t);
     }
     if (best) *best = opt_t;
     return opt;
@@ -260,12 +265,12 @@ static int64_t tune_heavy(const std::vector<int32_t> &len, int64_t nnz, const Bu
         rank_rows(len, H, rr, rc, rl);
         double tm = 0.0;
         int64_t WL = alg2_search(rl.data(), (int64_t)rl.size(), nnz, prm.max_warps,
-                                 prm.layout_rule, t, &tm);
+                                 prm.layout_rule, prm.max_rows, t, &tm);
         double chunks = 0.0;
         for (int32_t L : len)
             if (L > H) chunks += (double)((L + H - 1) / H);
         double cost = model_time(rl.data(), (int64_t)rl.size(), WL, prm.max_warps,
-                                 prm.layout_rule, t) + prm.split_cost * chunks;
+                                 prm.layout_rule, prm.max_rows, t) + prm.split_cost * chunks;
         if (cost < best) { best = cost; bestH = H; }
     }
     return bestH;
@@ -290,17 +295,25 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
         collen[(size_t)j] = src.colptr[j + 1] - src.colptr[j];
         maxlen = std::max(maxlen, collen[(size_t)j]);
     }
+    // (per segment when the matrix is a block-diagonal union of graphs)
     {
-        std::vector<int64_t> start((size_t)maxlen + 2, 0);
-        for (int64_t j = 0; j < N; ++j) start[(size_t)collen[(size_t)j]]++;
-        int64_t run = 0;
-        for (int64_t l = maxlen; l >= 0; --l) { int64_t c = start[(size_t)l]; start[(size_t)l] = run; run += c; }
+        const int64_t nseg = prm.nseg > 0 ? prm.nseg : 1;
+        std::vector<int64_t> start((size_t)maxlen + 2);
         L.perm.assign((size_t)N, 0);
         L.inv.assign((size_t)N, 0);
-        for (int64_t j = 0; j < N; ++j) {
-            int64_t p = start[(size_t)collen[(size_t)j]]++;
-            L.perm[(size_t)j] = (int32_t)p;
-            L.inv[(size_t)p] = (int32_t)j;
+        for (int64_t g = 0; g < nseg; ++g) {
+            const int64_t a = prm.nseg > 0 ? prm.seg_off[g] : 0;
+            const int64_t b = prm.nseg > 0 ? prm.seg_off[g + 1] : N;
+            std::fill(start.begin(), start.end(), 0);
+            for (int64_t j = a; j < b; ++j) start[(size_t)collen[(size_t)j]]++;
+            int64_t run = a, nz = start[0];
+            for (int64_t l = maxlen; l >= 0; --l) { int64_t c = start[(size_t)l]; start[(size_t)l] = run; run += c; }
+            for (int64_t j = a; j < b; ++j) {
+                int64_t p = start[(size_t)collen[(size_t)j]]++;
+                L.perm[(size_t)j] = (int32_t)p;
+                L.inv[(size_t)p] = (int32_t)j;
+            }
+            L.seg_dstart.push_back(b - nz);
         }
     }
     // zero-length columns sort last: dangling tail of the order
@@ -446,13 +459,14 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
         double tm = 0.0;
         int64_t WL = prm.wl > 0 ? prm.wl
                                 : alg2_search(rank_len[p].data(), nv, pn, prm.max_warps,
-                                              prm.layout_rule, table, &tm);
+                                              prm.layout_rule, prm.max_rows, table, &tm);
         if (prm.wl > 0)
-            tm = model_time(rank_len[p].data(), nv, WL, prm.max_warps, prm.layout_rule, table);
+            tm = model_time(rank_len[p].data(), nv, WL, prm.max_warps, prm.layout_rule,
+                            prm.max_rows, table);
         ph.wl = nv > 0 ? WL : 0;
         ph.predicted_s = tm;
         for (int64_t i = 0; i < nv;) {
-            int64_t w = rank_len[p][(size_t)i], h = wl_height(WL, w, nv - i);
+            int64_t w = rank_len[p][(size_t)i], h = wl_height(WL, w, nv - i, prm.max_rows);
             wfirst[p].push_back(i);
             wh[p].push_back((int32_t)h);
             ww[p].push_back((int32_t)w);

@@ -23,6 +23,9 @@
 
 using namespace spg;
 
+// Default cap on the rows of one workload (spg_build_opts.max_rows = 0).
+static constexpr int64_t kDefaultMaxRows = 256;
+
 static thread_local std::string g_err;
 
 static spg_status fail(spg_status s, const std::string &msg)
@@ -90,6 +93,13 @@ struct spg_format_t {
     uint8_t *d_dangling = nullptr;
     // HITS: per permuted position, 1 if in the hub half
     uint8_t *d_row_half = nullptr;
+    // BATCH: graph offsets and per-graph state
+    int ngraph = 0;
+    std::vector<int64_t> goff;
+    int64_t *d_goff = nullptr, *d_gdstart = nullptr;
+    int32_t *d_gid = nullptr, *d_giters = nullptr;
+    float *d_gbase = nullptr;
+    double *d_gl1 = nullptr, *d_gdelta = nullptr;
     // WEIGHTED: A on the device and the current transition weights
     int64_t *d_arp = nullptr;
     int32_t *d_acol = nullptr;
@@ -114,7 +124,7 @@ struct spg_format_t {
         DevBuf<uint32_t> sched;  // staged-kernel counters, 2 per part (zero between launches)
     } rt_fwd, rt_bwd;
     int64_t stage_cols = kStagedMaxCols;
-    int32_t pf_ahead = 8192;     // L2 bulk-prefetch distance of the slot stream (bytes)
+    int32_t pf_ahead = 0;        // L2 bulk-prefetch distance of the slot stream (bytes, 0 = off)
     int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
     int num_sms = 152;
     std::map<std::string, LoopGraph> graphs;
@@ -149,6 +159,8 @@ struct spg_format_t {
         if (bwd) bwd->free_device();
         cudaFree(d_rp); cudaFree(d_col); cudaFree(d_val); cudaFree(d_dangling);
         cudaFree(d_row_half); cudaFree(d_arp); cudaFree(d_acol); cudaFree(d_P);
+        cudaFree(d_goff); cudaFree(d_gdstart); cudaFree(d_gid); cudaFree(d_giters);
+        cudaFree(d_gbase); cudaFree(d_gl1); cudaFree(d_gdelta);
         x.release(); y.release(); stage_in.release(); stage_out.release(); red.release();
         rt_fwd.sched.release();
         rt_bwd.sched.release();
@@ -275,6 +287,26 @@ static int64_t query_max_warps()
 
 // ----------------------------------------------------------------- build --
 
+// Upload the forward layout and set up the launch-time state of a handle.
+static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream_t s)
+{
+    cudaError_t e = upload_layout(h->fwd, o.keep_plan != 0, s);
+    if (e == cudaErrorMemoryAllocation) return fail(SPG_ERR_OOM, "device memory for the format");
+    if (e != cudaSuccess) return cuda_fail(e, "upload");
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->stage_cols = o.x_stage_cols < 0 ? 0
+                  : (o.x_stage_cols > 0 ? std::min<int64_t>(o.x_stage_cols, kStagedMaxCols) : kStagedMaxCols);
+    h->pf_ahead = o.slab_prefetch > 0 ? (int32_t)std::min<int64_t>(o.slab_prefetch, 1 << 20) : 0;
+    h->pf_ahead = (h->pf_ahead + 255) / 256 * 256;
+    h->loop_mode = o.loop_mode == 1 ? 1 : 0;
+    CK(h->rt_fwd.sched.ensure(2 * h->fwd.parts.size()));
+    CK(cudaMemset(h->rt_fwd.sched.p, 0, 2 * h->fwd.parts.size() * sizeof(uint32_t)));
+    CK(cudaMalloc((void **)&h->d_state, sizeof(IterState)));
+    CK(cudaEventCreate(&h->ev0));
+    CK(cudaEventCreate(&h->ev1));
+    return SPG_OK;
+}
+
 extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
                                        const spg_build_opts *opts_in, void *stream,
                                        spg_handle *out)
@@ -320,6 +352,7 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
         prm.heavy = o.heavy_row;
         prm.layout_rule = o.layout_rule == 0 ? 0 : 1;
         prm.max_warps = o.max_warps > 0 ? o.max_warps : (h->host_only ? 9728 : query_max_warps());
+        prm.max_rows = o.max_rows < 0 ? 0 : (o.max_rows > 0 ? o.max_rows : kDefaultMaxRows);
         if (o.split_cost > 0) prm.split_cost = o.split_cost;
         prm.keep_plan = o.keep_plan != 0;
         prm.track_edges = kind == SPG_KIND_WEIGHTED;
@@ -386,20 +419,9 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
         if (!build_layout(src, prm, h->fwd, err)) return fail(SPG_ERR_INVALID, err);
 
         if (!h->host_only) {
-            cudaError_t e = upload_layout(h->fwd, o.keep_plan != 0, s);
-            if (e == cudaErrorMemoryAllocation) return fail(SPG_ERR_OOM, "device memory for the format");
-            if (e != cudaSuccess) return cuda_fail(e, "upload");
+            st = device_setup(h.get(), o, s);
+            if (st != SPG_OK) return st;
             const int64_t N = h->fwd.n;
-            cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-            h->stage_cols = o.x_stage_cols < 0 ? 0 : (o.x_stage_cols > 0 ? std::min<int64_t>(o.x_stage_cols, kStagedMaxCols) : kStagedMaxCols);
-            h->pf_ahead = o.slab_prefetch < 0 ? 0 : (o.slab_prefetch > 0 ? (int32_t)std::min<int64_t>(o.slab_prefetch, 1 << 20) : 8192);
-            h->pf_ahead = (h->pf_ahead + 255) / 256 * 256;
-            h->loop_mode = o.loop_mode == 1 ? 1 : 0;
-            CK(h->rt_fwd.sched.ensure(2 * h->fwd.parts.size()));
-            CK(cudaMemset(h->rt_fwd.sched.p, 0, 2 * h->fwd.parts.size() * sizeof(uint32_t)));
-            CK(cudaMalloc((void **)&h->d_state, sizeof(IterState)));
-            CK(cudaEventCreate(&h->ev0));
-            CK(cudaEventCreate(&h->ev1));
             if (kind == SPG_KIND_HITS) {
                 std::vector<uint8_t> half((size_t)N);
                 for (int64_t k = 0; k < N; ++k) half[(size_t)k] = h->fwd.inv[(size_t)k] >= n ? 1 : 0;
@@ -439,7 +461,7 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
                     ts.row_class = dcls.data();
                     h->bwd.reset(new Layout());
                     if (!build_layout(ts, prm, *h->bwd, err)) return fail(SPG_ERR_INVALID, err);
-                    e = upload_layout(*h->bwd, o.keep_plan != 0, s);
+                    cudaError_t e = upload_layout(*h->bwd, o.keep_plan != 0, s);
                     if (e != cudaSuccess) return cuda_fail(e, "upload transpose");
                     CK(h->rt_bwd.sched.ensure(2 * h->bwd->parts.size()));
                     CK(cudaMemset(h->rt_bwd.sched.p, 0, 2 * h->bwd->parts.size() * sizeof(uint32_t)));
@@ -1181,13 +1203,170 @@ extern "C" spg_status spg_rwr_adjoint(spg_handle h, float restart, int32_t seed,
     return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
 }
 
-extern "C" spg_status spg_batch_pagerank(const spg_handle *graphs, int count, float damping,
-                                         double tol, int max_iter, float *const *p_out,
-                                         spg_iter_info *info, void *stream)
+extern "C" spg_status spg_build_batch(const spg_csr *graphs, int count,
+                                      const spg_build_opts *opts_in, void *stream, spg_handle *out)
 {
-    (void)graphs; (void)count; (void)damping; (void)tol; (void)max_iter; (void)p_out;
-    (void)info; (void)stream;
-    return fail(SPG_ERR_UNSUPPORTED, "batched pagerank not built yet");
+    try {
+        if (!out || !graphs || count < 1) return fail(SPG_ERR_INVALID, "bad batch arguments");
+        *out = nullptr;
+        spg_build_opts o;
+        std::memset(&o, 0, sizeof o);
+        o.heavy_row = -1;
+        o.layout_rule = 1;
+        if (opts_in) o = *opts_in;
+        cudaStream_t s = (cudaStream_t)stream;
+        std::unique_ptr<spg_format_t> h(new spg_format_t());
+        h->kind = SPG_KIND_BATCH;
+        h->host_only = o.device < 0;
+        h->ngraph = count;
+        h->goff.assign((size_t)count + 1, 0);
+        std::vector<std::vector<int64_t>> hrp((size_t)count);
+        std::vector<std::vector<int32_t>> hcol((size_t)count);
+        std::vector<std::vector<float>> hval((size_t)count);
+        std::vector<const int64_t *> rps((size_t)count);
+        std::vector<const int32_t *> cols((size_t)count);
+        int64_t nnz = 0;
+        for (int g = 0; g < count; ++g) {
+            const float *v;
+            spg_status st = check_csr(&graphs[g], hrp[(size_t)g], hcol[(size_t)g], hval[(size_t)g],
+                                      rps[(size_t)g], cols[(size_t)g], v);
+            if (st != SPG_OK) return fail(st, "graph " + std::to_string(g) + ": " + g_err);
+            h->goff[(size_t)g + 1] = h->goff[(size_t)g] + graphs[g].n_rows;
+            nnz += graphs[g].nnz;
+        }
+        const int64_t N = h->goff[(size_t)count];
+        if (N >= kMaxN) return fail(SPG_ERR_INVALID, "total nodes must be < 2^28");
+        h->n_graph = N;
+        h->nnz_in = nnz;
+        // union column source of M: column off_g + u is row u of A_g, values 1/outdeg
+        std::vector<int64_t> cp((size_t)N + 1, 0);
+        std::vector<int32_t> ri((size_t)nnz);
+        std::vector<float> cv((size_t)nnz);
+        int64_t q = 0;
+        for (int g = 0; g < count; ++g) {
+            const int64_t off = h->goff[(size_t)g], ng = graphs[g].n_rows;
+            const int64_t *rp = rps[(size_t)g];
+            const int32_t *col = cols[(size_t)g];
+            for (int64_t u = 0; u < ng; ++u) {
+                const int64_t deg = rp[u + 1] - rp[u];
+                const float w = deg > 0 ? (float)(1.0 / (double)deg) : 0.f;
+                for (int64_t k = rp[u]; k < rp[u + 1]; ++k) {
+                    ri[(size_t)q] = (int32_t)(off + col[k]);
+                    cv[(size_t)q] = w;
+                    ++q;
+                }
+                cp[(size_t)(off + u) + 1] = q;
+            }
+        }
+        ColumnSource src;
+        src.n = N; src.colptr = cp.data(); src.rowidx = ri.data(); src.val = cv.data();
+        if (!h->host_only) CK(cudaGetDevice(&h->device));
+        BuildParams prm;
+        prm.tile_width = 0;
+        prm.wl = o.wl;
+        prm.heavy = o.heavy_row;
+        prm.layout_rule = o.layout_rule == 0 ? 0 : 1;
+        prm.max_warps = o.max_warps > 0 ? o.max_warps : (h->host_only ? 9728 : query_max_warps());
+        prm.max_rows = o.max_rows < 0 ? 0 : (o.max_rows > 0 ? o.max_rows : kDefaultMaxRows);
+        if (o.split_cost > 0) prm.split_cost = o.split_cost;
+        prm.keep_plan = o.keep_plan != 0;
+        prm.seg_off = h->goff.data();
+        prm.nseg = count;
+        std::string err;
+        if (!build_layout(src, prm, h->fwd, err)) return fail(SPG_ERR_INVALID, err);
+        if (!h->host_only) {
+            spg_status st = device_setup(h.get(), o, s);
+            if (st != SPG_OK) return st;
+            std::vector<int32_t> gid((size_t)N);
+            for (int g = 0; g < count; ++g)
+                for (int64_t v = h->goff[(size_t)g]; v < h->goff[(size_t)g + 1]; ++v) gid[(size_t)v] = g;
+            CK(upload(&h->d_gid, gid.data(), gid.size()));
+            CK(upload(&h->d_goff, h->goff.data(), h->goff.size()));
+            CK(upload(&h->d_gdstart, h->fwd.seg_dstart.data(), h->fwd.seg_dstart.size()));
+            CK(cudaMalloc((void **)&h->d_giters, count * sizeof(int32_t)));
+            CK(cudaMalloc((void **)&h->d_gbase, count * sizeof(float)));
+            CK(cudaMalloc((void **)&h->d_gl1, count * sizeof(double)));
+            CK(cudaMalloc((void **)&h->d_gdelta, count * sizeof(double)));
+        }
+        *out = h.release();
+        return SPG_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(SPG_ERR_OOM, "host memory");
+    } catch (const std::exception &ex) {
+        return fail(SPG_ERR_INVALID, ex.what());
+    }
+}
+
+extern "C" spg_status spg_batch_offsets(spg_handle h, int64_t *offsets)
+{
+    if (!h || h->kind != SPG_KIND_BATCH || !offsets) return fail(SPG_ERR_INVALID, "needs a batch handle");
+    std::memcpy(offsets, h->goff.data(), h->goff.size() * sizeof(int64_t));
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_batch_pagerank(spg_handle h, float damping, double tol, int max_iter,
+                                         float *p_out, spg_iter_info *info, void *stream)
+{
+    if (!h || h->host_only || h->kind != SPG_KIND_BATCH) return fail(SPG_ERR_UNSUPPORTED, "needs a batch handle");
+    if (!p_out || !(damping >= 0.f && damping < 1.f) || max_iter < 0)
+        return fail(SPG_ERR_INVALID, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->fwd.n;
+    const int G = h->ngraph;
+    spg_status st = ensure_vectors(h, N);
+    if (st != SPG_OK) return st;
+    const double c = damping;
+    IterState hs = make_state(h, c, tol, max_iter, N, h->x.p, h->y.p);
+    hs.gid = h->d_gid;
+    hs.gbase = h->d_gbase;
+    hs.gl1 = h->d_gl1;
+    hs.gdelta = h->d_gdelta;
+    hs.giters = h->d_giters;
+    hs.goff = h->d_goff;
+    hs.gdstart = h->d_gdstart;
+    hs.ngraph = G;
+    CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(h->d_giters, 0, G * sizeof(int32_t), s));
+    // p(0) = 1/n_g: its dangling mass is (#dangling_g)/n_g
+    std::vector<float> base((size_t)G);
+    for (int g = 0; g < G; ++g) {
+        const double ng = (double)(h->goff[(size_t)g + 1] - h->goff[(size_t)g]);
+        const double nd = (double)(h->goff[(size_t)g + 1] - h->fwd.seg_dstart[(size_t)g]);
+        base[(size_t)g] = (float)((c * (nd / ng) + (1.0 - c)) / ng);
+    }
+    CK(cudaMemcpyAsync(h->d_gbase, base.data(), G * sizeof(float), cudaMemcpyHostToDevice, s));
+    launch_batch_init(N, h->d_state, h->x.p, s);
+    LoopGraph *lg;
+    st = get_loop_graph(h, "batch", [&](cudaStream_t cs, unsigned long long cond, int uc) {
+        launch_parts(h, EPI_BATCH, nullptr, nullptr, h->d_state, h->red.p, cs);
+        launch_batch_reduce(h->d_state, G, cs);
+        launch_batch_check(h->d_state, G, cond, uc, cs);
+    }, &lg);
+    if (st != SPG_OK) return st;
+    CK(cudaGetLastError());
+    if ((st = run_loop(h, lg, max_iter, &hs, nullptr, s)) != SPG_OK) return st;
+    const bool out_host = !is_device_ptr(p_out);
+    float *od = p_out;
+    if (out_host) { CK(h->stage_out.ensure((size_t)N)); od = h->stage_out.p; }
+    launch_scatter_state(N, h->fwd.d_inv, h->d_state, od, nullptr, 0, s);
+    if (out_host) CK(cudaMemcpyAsync(p_out, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> it((size_t)G);
+    std::vector<double> l1((size_t)G), dg((size_t)G);
+    CK(cudaMemcpyAsync(it.data(), h->d_giters, G * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(l1.data(), h->d_gl1, G * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(dg.data(), h->d_gdelta, G * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int g = 0; g < G; ++g) {
+        if (it[(size_t)g] == 0) all = false;
+        if (info) {
+            info[g].iters = it[(size_t)g] ? it[(size_t)g] : hs.iter;
+            info[g].last_l1 = l1[(size_t)g];
+            info[g].dangling = dg[(size_t)g];
+            info[g].ms = 0.f;
+        }
+    }
+    return (tol > 0 && !all) ? SPG_NOT_CONVERGED : SPG_OK;
 }
 
 // ------------------------------------------------------------------ misc --

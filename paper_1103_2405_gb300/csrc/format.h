@@ -31,9 +31,14 @@ struct BuildParams {
     int64_t heavy = -1;
     int layout_rule = 1;
     int64_t max_warps = 9728;
+    int64_t max_rows = 0;     // > 0: at most this many rows per workload
     double split_cost = 2e-7;
     bool keep_plan = false;
     bool track_edges = false;
+    // block-diagonal union of independent graphs: node segments
+    // [seg_off[g], seg_off[g+1]); the degree order is taken within each segment
+    const int64_t *seg_off = nullptr;
+    int64_t nseg = 0;
 };
 
 struct PartHost {
@@ -58,6 +63,7 @@ struct Layout {
     int64_t nsplit = 0, nchunk_slots = 0, nred = 0;
     int64_t dangling_start = 0;
     std::vector<int32_t> perm, inv;
+    std::vector<int64_t> seg_dstart;    // per segment: first position of its dangling tail
     std::vector<PartHost> parts;
     std::vector<int64_t> zero_rows;
     // packed arrays (host copy; released after upload unless kept)
@@ -106,9 +112,9 @@ cudaError_t upload_layout(Layout &L, bool keep_host, cudaStream_t stream);
 
 // Algorithm 3 model (seconds) of one ranked part; Algorithm 2 search.
 double model_time(const int32_t *vlen, int64_t nv, int64_t WL, int64_t max_warps, int rule,
-                  const PerfTable &t);
+                  int64_t max_rows, const PerfTable &t);
 int64_t alg2_search(const int32_t *vlen, int64_t nv, int64_t nnz, int64_t max_warps,
-                    int rule, const PerfTable &t, double *best);
+                    int rule, int64_t max_rows, const PerfTable &t, double *best);
 
 int hw_threads();
 

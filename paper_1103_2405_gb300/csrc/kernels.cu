@@ -63,6 +63,8 @@ struct Epi {
     float sc[2];
     int hnorm;
     const float *aux;
+    const int32_t *gid;
+    const float *gbase;
 };
 
 template <int MODE>
@@ -70,8 +72,12 @@ __device__ __forceinline__ Epi load_epi(const IterState *st)
 {
     Epi E;
     E.c = 1.f; E.base = 0.f; E.tele = 0.f; E.seed = -1; E.dstart = 0;
-    E.sc[0] = E.sc[1] = 1.f; E.hnorm = 2; E.aux = nullptr;
-    if (MODE == EPI_ADJ) {
+    E.sc[0] = E.sc[1] = 1.f; E.hnorm = 2; E.aux = nullptr; E.gid = nullptr; E.gbase = nullptr;
+    if (MODE == EPI_BATCH) {
+        E.c = (float)st->c;
+        E.gid = st->gid;
+        E.gbase = st->gbase;
+    } else if (MODE == EPI_ADJ) {
         E.c = (float)st->c;
         E.seed = st->seed;
         E.aux = st->aux;
@@ -106,6 +112,8 @@ __device__ __forceinline__ void epilogue(const Epi &E, uint32_t rid, float tot,
         y[v] = f;
         r0 += fabs((double)f - (double)x[v]);
         if ((int64_t)v >= E.dstart) r1 += (double)f;
+    } else if (MODE == EPI_BATCH) {
+        y[v] = fmaf(E.c, tot, __ldg(E.gbase + __ldg(E.gid + v)));
     } else if (MODE == EPI_ADJ) {
         // lambda = c K^T lambda + g with K^T = M^T + 1_D e_s^T: dangling rows
         // (class bit) also receive c * lambda_s
@@ -142,7 +150,7 @@ __device__ __noinline__ void finish_split(const Epi &E, const SplitView &sv, dou
     sv.counter[s] = 0u;
     double r0 = 0.0, r1 = 0.0;
     epilogue<MODE>(E, sr.row, tot, x, y, r0, r1);
-    if (MODE != EPI_RAW) red[sv.red_split_base + sr.red_slot] = make_double2(r0, r1);
+    if (MODE != EPI_RAW && MODE != EPI_BATCH) red[sv.red_split_base + sr.red_slot] = make_double2(r0, r1);
 }
 
 template <int MODE>
@@ -262,23 +270,52 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
             if (pf.ahead) pf.advance((unsigned)((int64_t)(i + 1) * d.w * 8), lane);
         }
     } else {
-        // column-major (ELL): one row per lane, 32-row blocks
-        for (int b = 0; b < hp; b += 32) {
-            const uint2 *s = slab + (int64_t)b * d.w + lane;
-            float acc = 0.f;
+        // column-major (ELL): one row per lane; two 32-row blocks per pass so
+        // each lane keeps two independent load chains in flight
+        for (int b = 0; b < hp; b += 64) {
+            const bool two = b + 32 < hp;
+            const uint2 *sa = slab + (int64_t)b * d.w + lane;
+            const uint2 *sb = sa + (int64_t)32 * d.w;
+            float acc_a = 0.f, acc_b = 0.f;
             int e = 0;
-            for (; e + 7 < d.w; e += 8) {
-                if (pf.ahead) pf.advance((unsigned)(((int64_t)b * d.w + (int64_t)e * 32) * 8), lane);
-                uint2 a[8];
+            if (two) {
+                for (; e + 3 < d.w; e += 4) {
+                    if (pf.ahead) pf.advance((unsigned)(((int64_t)b * d.w + (int64_t)e * 32) * 8), lane);
+                    uint2 a[4], c[4];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) a[u] = __ldcs(s + (int64_t)(e + u) * 32);
+                    for (int u = 0; u < 4; ++u) {
+                        a[u] = __ldcs(sa + (int64_t)(e + u) * 32);
+                        c[u] = __ldcs(sb + (int64_t)(e + u) * 32);
+                    }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc = slot_fma_g(a[u], g, acc);
+                    for (int u = 0; u < 4; ++u) {
+                        acc_a = slot_fma_g(a[u], g, acc_a);
+                        acc_b = slot_fma_g(c[u], g, acc_b);
+                    }
+                }
+                for (; e < d.w; ++e) {
+                    const uint2 a0 = __ldcs(sa + (int64_t)e * 32), c0 = __ldcs(sb + (int64_t)e * 32);
+                    acc_a = slot_fma_g(a0, g, acc_a);
+                    acc_b = slot_fma_g(c0, g, acc_b);
+                }
+            } else {
+                for (; e + 7 < d.w; e += 8) {
+                    if (pf.ahead) pf.advance((unsigned)(((int64_t)b * d.w + (int64_t)e * 32) * 8), lane);
+                    uint2 a[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) a[u] = __ldcs(sa + (int64_t)(e + u) * 32);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc_a = slot_fma_g(a[u], g, acc_a);
+                }
+                for (; e < d.w; ++e) acc_a = slot_fma_g(__ldcs(sa + (int64_t)e * 32), g, acc_a);
             }
-            for (; e < d.w; ++e) acc = slot_fma_g(__ldcs(s + (int64_t)e * 32), g, acc);
-            const int i = b + lane;
-            if (i < d.h) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc, x, y, r0, r1);
-            if (pf.ahead) pf.advance((unsigned)((int64_t)(b + 32) * d.w * 8), lane);
+            int i = b + lane;
+            if (i < d.h) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc_a, x, y, r0, r1);
+            if (two) {
+                i += 32;
+                if (i < d.h) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc_b, x, y, r0, r1);
+            }
+            if (pf.ahead) pf.advance((unsigned)((int64_t)(b + 64) * d.w * 8), lane);
         }
     }
 }
@@ -311,7 +348,7 @@ k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restri
         const GatherGlobal g{x};
         do_workload<MODE>(pv.wl[wid], pv, sv, g, E, x, y, red, lane, r0, r1);
     }
-    if (MODE != EPI_RAW) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
+    if (MODE != EPI_RAW && MODE != EPI_BATCH) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
 }
 
 // Same computation with the part's densest x columns staged in shared
@@ -357,7 +394,7 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
             pv.sched[1] = 0u;
         }
     }
-    if (MODE != EPI_RAW) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
+    if (MODE != EPI_RAW && MODE != EPI_BATCH) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
 }
 
 int part_blocks_per_sm()
@@ -392,6 +429,7 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
         case EPI_PAGERANK: launch_staged<EPI_PAGERANK>(pv, sv, x, y, st, red, s); break;
         case EPI_RWR: launch_staged<EPI_RWR>(pv, sv, x, y, st, red, s); break;
         case EPI_ADJ: launch_staged<EPI_ADJ>(pv, sv, x, y, st, red, s); break;
+        case EPI_BATCH: launch_staged<EPI_BATCH>(pv, sv, x, y, st, red, s); break;
         default: launch_staged<EPI_HITS>(pv, sv, x, y, st, red, s); break;
         }
         count_launches(1);
@@ -403,6 +441,7 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
     case EPI_PAGERANK: k_part<EPI_PAGERANK><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     case EPI_RWR: k_part<EPI_RWR><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     case EPI_ADJ: k_part<EPI_ADJ><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
+    case EPI_BATCH: k_part<EPI_BATCH><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     default: k_part<EPI_HITS><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     }
     count_launches(1);
@@ -787,6 +826,102 @@ void launch_init_delta_k(const IterState *st, const float *X, int k, double *del
     count_launches(1);
 }
 
+// ------------------------------------------------------- batch of graphs --
+
+// Block g: L1 change and dangling mass of graph g over its positions
+// [goff[g], goff[g+1]) (its dangling tail starts at gdstart[g]); fixed order.
+__global__ void __launch_bounds__(256) k_batch_reduce(IterState *st)
+{
+    const int g = blockIdx.x;
+    const float *x = st->buf[st->parity];
+    const float *y = st->buf[st->parity ^ 1];
+    const int64_t a = st->goff[g], b = st->goff[g + 1], ds = st->gdstart[g];
+    double l1 = 0.0, dg = 0.0;
+    for (int64_t v = a + threadIdx.x; v < b; v += blockDim.x) {
+        const float f = y[v];
+        l1 += fabs((double)f - (double)x[v]);
+        if (v >= ds) dg += (double)f;
+    }
+    __shared__ double s0[8], s1[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    l1 = warp_sum_d(l1);
+    dg = warp_sum_d(dg);
+    if (lane == 0) { s0[warp] = l1; s1[warp] = dg; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double p = 0.0, q = 0.0;
+        for (int w = 0; w < 8; ++w) { p += s0[w]; q += s1[w]; }
+        st->gl1[g] = p;
+        st->gdelta[g] = q;
+    }
+}
+
+void launch_batch_reduce(IterState *st, int ngraph, cudaStream_t s)
+{
+    k_batch_reduce<<<ngraph, 256, 0, s>>>(st);
+    count_launches(1);
+}
+
+// Per graph: the next base (c * dangling mass + 1 - c) / n_g and the
+// iteration its L1 change first went below tol; the loop stops when every
+// graph has converged or at max_iter.
+__global__ void __launch_bounds__(1024) k_batch_check(IterState *st, int ngraph,
+                                                      cudaGraphConditionalHandle cond, int use_cond)
+{
+    if (st->done) return;
+    __shared__ double smax[32];
+    __shared__ int sall[32];
+    const double c = st->c, tol = st->tol;
+    const int it = st->iter + 1;
+    double mx = 0.0;
+    int all = 1;
+    for (int g = threadIdx.x; g < ngraph; g += blockDim.x) {
+        const double l1 = st->gl1[g];
+        const double ng = (double)(st->goff[g + 1] - st->goff[g]);
+        st->gbase[g] = (float)((c * st->gdelta[g] + (1.0 - c)) / ng);
+        if (tol > 0.0 && l1 < tol) {
+            if (st->giters[g] == 0) st->giters[g] = it;
+        } else {
+            all = 0;
+        }
+        mx = fmax(mx, l1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
+        all &= __shfl_xor_sync(kFull, all, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { smax[warp] = mx; sall[warp] = all; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        int a = 1;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { m = fmax(m, smax[w]); a &= sall[w]; }
+        st->l1 = m;
+        st->iter = it;
+        st->parity ^= 1;
+        const int done = it >= st->max_iter || (tol > 0.0 && a);
+        st->done = done;
+        if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
+    }
+}
+
+void launch_batch_check(IterState *st, int ngraph, unsigned long long cond, int use_cond,
+                        cudaStream_t s)
+{
+    k_batch_check<<<1, 1024, 0, s>>>(st, ngraph, (cudaGraphConditionalHandle)cond, use_cond);
+    count_launches(1);
+}
+
+__global__ void k_batch_init(int64_t n, const IterState *__restrict__ st, float *__restrict__ x)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int g = st->gid[v];
+        x[v] = (float)(1.0 / (double)(st->goff[g + 1] - st->goff[g]));
+    }
+}
+
 // ------------------------------------------------------------- vectors --
 
 static inline int grid_for(int64_t n, int per = 256)
@@ -895,6 +1030,12 @@ __global__ void k_fill(int64_t n, float v, float *__restrict__ p)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
+}
+
+void launch_batch_init(int64_t n, const IterState *st, float *x, cudaStream_t s)
+{
+    k_batch_init<<<grid_for(n), 256, 0, s>>>(n, st, x);
+    count_launches(1);
 }
 
 void launch_fill(int64_t n, float v, float *p, cudaStream_t s)

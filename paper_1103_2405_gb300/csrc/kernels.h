@@ -12,7 +12,8 @@ enum EpiMode {
     EPI_PAGERANK = 1,  // y' = c (M' x')_v + (c delta + 1 - c)/n;  sum |y'-x'|, dangling sum
     EPI_RWR = 2,       // y' = c (M' x')_v + [v == s](c delta + 1 - c); same sums
     EPI_HITS = 3,      // y' = (M' x')_v * scale[other half];  per-half sum or sum of squares
-    EPI_ADJ = 4        // y' = c (M'^T x')_v + [v dangling] c x'_s + g'_v;  sum |y'-x'|
+    EPI_ADJ = 4,       // y' = c (M'^T x')_v + [v dangling] c x'_s + g'_v;  sum |y'-x'|
+    EPI_BATCH = 5      // y' = c (M' x')_v + base[graph of v];  sums in a separate pass
 };
 
 // One tiled-composite launch of one part (Solution 3: one warp per
@@ -82,6 +83,15 @@ void launch_edge_grad(int64_t n, const int64_t *a_rp, const int32_t *a_col, cons
 
 // Resident blocks per SM of the tiled-composite SpMV kernel on this device.
 int part_blocks_per_sm();
+
+// Batch of graphs: per-graph L1 change and dangling mass (one block per
+// graph, fixed order), then the per-graph bases, convergence record and the
+// loop condition (one block).
+void launch_batch_reduce(IterState *st, int ngraph, cudaStream_t s);
+void launch_batch_check(IterState *st, int ngraph, unsigned long long cond, int use_cond,
+                        cudaStream_t s);
+// x[v] = 1 / n_{graph of v}
+void launch_batch_init(int64_t n, const IterState *st, float *x, cudaStream_t s);
 
 // Launch counter of this library.
 void count_launches(int64_t k);

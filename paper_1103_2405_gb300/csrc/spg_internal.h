@@ -93,6 +93,16 @@ struct IterState {
     int64_t dangling_start;
     float *buf[2];        // ping-pong iterates (permuted order)
     const float *aux;     // adjoint: the loss gradient g in permuted order
+    // batch of independent graphs (block-diagonal union)
+    const int32_t *gid;   // graph of each permuted position
+    float *gbase;         // per graph: (c * dangling mass + 1 - c) / n_g of the current iterate
+    double *gl1;          // per graph: L1 change of the last iteration
+    double *gdelta;       // per graph: dangling mass of the current iterate
+    int32_t *giters;      // per graph: iterations until its L1 change went below tol (0 = not yet)
+    const int64_t *goff;  // per graph: first position (count + 1 entries)
+    const int64_t *gdstart;  // per graph: first position of its dangling tail
+    int32_t ngraph;
+    int32_t pad2_;
 };
 
 }  // namespace spg

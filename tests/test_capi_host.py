@@ -53,26 +53,29 @@ def _table_file(perf, nlog=21):
     return path
 
 
-CASES = [  # (scale, ef, tile_width, heavy, rule, max_warps)
-    (12, 8, 256, -1, 1, 300),
-    (12, 8, 64, 0, 0, 97),
-    (12, 8, -1, -1, 1, 9728),
-    (12, 8, 1024, 64, 1, 50),
-    (10, 16, 128, -1, 0, 13),
+CASES = [  # (scale, ef, tile_width, heavy, rule, max_warps, max_rows)
+    (12, 8, 256, -1, 1, 300, -1),
+    (12, 8, 64, 0, 0, 97, -1),
+    (12, 8, -1, -1, 1, 9728, -1),
+    (12, 8, 1024, 64, 1, 50, -1),
+    (10, 16, 128, -1, 0, 13, -1),
+    (12, 8, -1, -1, 1, 9728, 256),
+    (12, 8, 512, -1, 1, 40, 37),
 ]
 
 
-@pytest.mark.parametrize("scale,ef,tw,heavy,rule,mw", CASES)
-def test_host_plan_matches_oracle(spg, scale, ef, tw, heavy, rule, mw):
+@pytest.mark.parametrize("scale,ef,tw,heavy,rule,mw,mr", CASES)
+def test_host_plan_matches_oracle(spg, scale, ef, tw, heavy, rule, mw, mr):
     nlog = 21
     perf = np.random.default_rng(scale * 7 + mw).uniform(1e9, 5e9, 2 * nlog * nlog)
     path = _table_file(perf)
     try:
         rp, col = graphgen.rmat(scale, ef, seed=1)
         f = spg.Format(rp, col, kind="pagerank", tile_width=tw, heavy_row=heavy, layout_rule=rule,
-                       max_warps=mw, keep_plan=True, host_only=True, table=path)
+                       max_warps=mw, keep_plan=True, host_only=True, table=path, max_rows=mr)
         plan = oracle.plan_format(rp, col, tile_width=max(tw, 0), max_warps=mw,
-                                  table=(nlog, perf), heavy=heavy, rule=rule, split_cost=2e-7)
+                                  table=(nlog, perf), heavy=heavy, rule=rule, split_cost=2e-7,
+                                  max_rows=max(mr, 0))
     finally:
         spg.load_table(None)
         os.unlink(path)
@@ -129,7 +132,7 @@ def test_malformed_csr_rejected(spg, bad):
         col = np.array([1, 2, 0, 0], np.int32)
     csr = spg._Csr(n, nc, nnz, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(col.ctypes.data),
                    None, 0)
-    opts = spg._Opts(0, 0, -1, 1, 64, 1, 0, 0, 0, -1, 0.0, None, 0, 0, 0)
+    opts = spg._Opts(0, 0, -1, 1, 64, 1, 0, 0, 0, -1, 0.0, None, 0, 0, 0, 0)
     h = ctypes.c_void_p()
     st = L.spg_build_format(ctypes.byref(csr), 1, ctypes.byref(opts), None, ctypes.byref(h))
     assert st == -1 and not h.value
@@ -146,6 +149,20 @@ def test_degenerate_graphs_build(spg):
         assert info["dangling_start"] == 0
         r, c, v = f.export_entries()
         assert r.size == 0
+
+
+def test_batch_host_build_orders_within_each_graph(spg):
+    graphs = [graphgen.chung_lu(n, 12 * n, 2.3, n / 4, seed=5 + i) for i, n in enumerate((300, 77, 1000))]
+    b = spg.BatchFormat(graphs, host_only=True, max_warps=64)
+    off = b.offsets
+    assert off.tolist() == [0, 300, 377, 1377]
+    pi = np.empty(b.n, np.int32)
+    inv = np.empty(b.n, np.int32)
+    spg._check(spg.lib().spg_format_perm(b._h, spg._ptr(pi)[0], spg._ptr(inv)[0]))
+    for g, (rp, col) in enumerate(graphs):
+        seg = inv[off[g]:off[g + 1]] - off[g]
+        p_ref, inv_ref = oracle.degree_order(np.diff(rp))
+        assert np.array_equal(seg, inv_ref)       # Solution 2 order within each graph
 
 
 def test_bad_table_rejected(spg):
