@@ -112,6 +112,7 @@ struct spg_format_t {
     DevBuf<int32_t> seeds;
     DevBuf<float> X, Y;
     DevBuf<float> aux, stage_r;
+    DevBuf<double> init_part;    // block partials of the start vector's dangling mass
     IterState *d_state = nullptr;
     // launch views of the parts: plain (8-warp blocks) and staged (x slice in smem)
     struct Views {
@@ -165,7 +166,7 @@ struct spg_format_t {
         rt_fwd.sched.release();
         rt_bwd.sched.release();
         redk.release(); delta_k.release(); l1_k.release(); partial_k.release(); seeds.release();
-        X.release(); Y.release(); aux.release(); stage_r.release();
+        X.release(); Y.release(); aux.release(); stage_r.release(); init_part.release();
         cudaFree(d_state);
         for (auto &kv : graphs) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -894,7 +895,8 @@ extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int 
     } else {
         launch_fill(N, (float)(1.0 / (double)N), h->x.p, s);
     }
-    launch_init_delta(h->d_state, s);
+    CK(h->init_part.ensure((size_t)init_delta_scratch()));
+        launch_init_delta(h->d_state, h->init_part.p, s);
     LoopGraph *g;
     const int nred = nred_of(h, get_views(h, true));
     st = get_loop_graph(h, "pagerank", [&](cudaStream_t cs, unsigned long long cond, int uc) {
@@ -979,7 +981,8 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
         CK(cudaMemcpyAsync(h->seeds.p, ps.data(), sizeof(int32_t), cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(h->x.p, 0, N * sizeof(float), s));
         launch_set_one(h->x.p, h->seeds.p, 1, s);
-        launch_init_delta(h->d_state, s);
+        CK(h->init_part.ensure((size_t)init_delta_scratch()));
+        launch_init_delta(h->d_state, h->init_part.p, s);
         st = get_loop_graph(h, "rwr1", [&](cudaStream_t cs, unsigned long long cond, int uc) {
             launch_parts(h, EPI_RWR, nullptr, nullptr, h->d_state, h->red.p, cs);
             launch_check(EPI_RWR, h->d_state, h->red.p, nred, cond, uc, cs);
@@ -1069,7 +1072,8 @@ extern "C" spg_status spg_baseline_pagerank(spg_handle h, spg_baseline which, fl
     IterState hs = make_state(h, damping, tol, max_iter, n, h->x.p, h->y.p);
     CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
     launch_fill(n, (float)(1.0 / (double)n), h->x.p, s);
-    launch_init_delta_flags(h->d_state, h->d_dangling, s);
+    CK(h->init_part.ensure((size_t)init_delta_scratch()));
+    launch_init_delta_flags(h->d_state, h->d_dangling, h->init_part.p, s);
     LoopGraph *g;
     const std::string key = which == SPG_BASELINE_CSR_SCALAR ? "pr_csr_scalar" : "pr_csr_vector";
     st = get_loop_graph(h, key, [&](cudaStream_t cs, unsigned long long cond, int uc) {

@@ -758,36 +758,55 @@ void launch_check_k(IterState *st, const double *redk, int nred, int k, double *
     count_launches(1);
 }
 
-__global__ void __launch_bounds__(1024) k_init_delta(IterState *st)
+// Dangling mass of the start vector: a deterministic two-stage sum (fixed
+// per-block ranges, then one block adds the block partials in order).
+constexpr int kInitBlocks = 304;
+
+template <bool FLAGS>
+__global__ void __launch_bounds__(256) k_init_delta_part(const IterState *st, const uint8_t *flags,
+                                                        double *part)
 {
     const float *x = st->buf[st->parity];
+    const int64_t a = FLAGS ? 0 : st->dangling_start, n = st->n;
+    const int64_t len = n - a, per = (len + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = a + per * blockIdx.x, hi = min(n, lo + per);
+    double s = 0.0;
+    for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x)
+        if (!FLAGS || flags[v]) s += (double)x[v];
+    __shared__ double sm[8];
+    s = warp_sum_d(s);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sm[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_init_delta_final(IterState *st, const double *part, int nb)
+{
     double a = 0.0, b = 0.0;
-    for (int64_t v = st->dangling_start + threadIdx.x; v < st->n; v += blockDim.x) a += x[v];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += part[i];
     block_sum2_1024(a, b);
     if (threadIdx.x == 0) st->delta = a;
 }
 
-void launch_init_delta(IterState *st, cudaStream_t s)
+void launch_init_delta(IterState *st, double *scratch, cudaStream_t s)
 {
-    k_init_delta<<<1, 1024, 0, s>>>(st);
-    count_launches(1);
+    k_init_delta_part<false><<<kInitBlocks, 256, 0, s>>>(st, nullptr, scratch);
+    k_init_delta_final<<<1, 1024, 0, s>>>(st, scratch, kInitBlocks);
+    count_launches(2);
 }
 
-__global__ void __launch_bounds__(1024) k_init_delta_flags(IterState *st, const uint8_t *dangling)
+void launch_init_delta_flags(IterState *st, const uint8_t *dangling, double *scratch, cudaStream_t s)
 {
-    const float *x = st->buf[st->parity];
-    double a = 0.0, b = 0.0;
-    for (int64_t v = threadIdx.x; v < st->n; v += blockDim.x)
-        if (dangling[v]) a += x[v];
-    block_sum2_1024(a, b);
-    if (threadIdx.x == 0) st->delta = a;
+    k_init_delta_part<true><<<kInitBlocks, 256, 0, s>>>(st, dangling, scratch);
+    k_init_delta_final<<<1, 1024, 0, s>>>(st, scratch, kInitBlocks);
+    count_launches(2);
 }
 
-void launch_init_delta_flags(IterState *st, const uint8_t *dangling, cudaStream_t s)
-{
-    k_init_delta_flags<<<1, 1024, 0, s>>>(st, dangling);
-    count_launches(1);
-}
+int init_delta_scratch() { return kInitBlocks; }
 
 __global__ void k_set_one(float *p, const int32_t *idx, int count)
 {

@@ -38,9 +38,12 @@ void launch_check(int mode, IterState *st, const double2 *red, int nred,
 void launch_check_k(IterState *st, const double *redk, int nred, int k, double *delta_k,
                     double *l1_k, unsigned long long cond, int use_cond, cudaStream_t s);
 
-// Dangling mass of buf[parity] (positions >= dangling_start) into st->delta.
-void launch_init_delta(IterState *st, cudaStream_t s);
-void launch_init_delta_flags(IterState *st, const uint8_t *dangling, cudaStream_t s);
+// Dangling mass of buf[parity] (positions >= dangling_start, or the rows
+// flagged in `dangling`) into st->delta; `scratch` holds init_delta_scratch()
+// doubles.
+void launch_init_delta(IterState *st, double *scratch, cudaStream_t s);
+void launch_init_delta_flags(IterState *st, const uint8_t *dangling, double *scratch, cudaStream_t s);
+int init_delta_scratch();
 // p[idx[i]] = 1 for i < count
 void launch_set_one(float *p, const int32_t *idx, int count, cudaStream_t s);
 void launch_init_delta_k(const IterState *st, const float *X, int k, double *delta_k,

@@ -33,8 +33,12 @@ def test_batch_pagerank_matches_oracle(opts):
     for g, ((rp, col), pg) in enumerate(zip(graphs, b.split(p))):
         p_star, it_ref, _ = oracle.pagerank(rp, col, 0.85, tol=1e-13)
         assert np.abs(pg - p_star).sum() <= 1e-6, g
-        _, it8, _ = oracle.pagerank(rp, col, 0.85, tol=1e-8)
-        assert abs(infos[g]["iters"] - it8) <= 2, (g, infos[g], it8)
+    # per-graph convergence iterations, at a tolerance well above the FP32
+    # noise floor of the L1 change of small graphs (n_g * ulp(p) ~ 1e-8)
+    _, infos6 = b.pagerank(0.85, tol=1e-6, max_iter=1000, like=torch.empty(0, device=DEV))
+    for g, (rp, col) in enumerate(graphs):
+        _, it6, _ = oracle.pagerank(rp, col, 0.85, tol=1e-6)
+        assert abs(infos6[g]["iters"] - it6) <= 1, (g, infos6[g], it6)
 
 
 def test_batch_fixed_iterations_equal_single_graph_runs():
