@@ -29,7 +29,16 @@ DAMPING = 0.85
 WORKLOADS = {
     "rmat22": dict(scale=22, ef=16, desc="R-MAT scale 22, edge factor 16, PageRank iteration"),
     "rmat26": dict(scale=26, ef=16, desc="R-MAT scale 26, edge factor 16, PageRank iteration"),
+    "chunglu50m": dict(cl=(50_000_000, 800_000_000, 2.1, 1_000_000),
+                       desc="Chung-Lu 50M nodes, ~800M edges, exponent 2.1, max degree 1M, "
+                            "PageRank iteration"),
     "rmat14": dict(scale=14, ef=8, desc="R-MAT scale 14, edge factor 8, PageRank iteration"),
+    "rwr64": dict(scale=22, ef=16, desc="R-MAT scale 22, edge factor 16, RWR with 64 restart "
+                                        "vectors as one SpMM iteration"),
+    "batch512": dict(desc="512 Chung-Lu graphs, n log-uniform in [2^10, 2^17], exponent 2.3, "
+                          "average degree 12, one batched PageRank iteration"),
+    "adjoint20": dict(scale=20, ef=16, desc="R-MAT scale 20, edge factor 16, softmax edge "
+                                            "weights, one adjoint (transposed SpMV) iteration"),
 }
 
 
@@ -113,7 +122,141 @@ class Clocks:
 def graph(workload):
     import graphgen
     w = WORKLOADS[workload]
+    if "cl" in w:
+        n, m, gamma, dmax = w["cl"]
+        return graphgen.chung_lu(n, m, gamma, dmax, seed=1)
     return graphgen.rmat(w["scale"], w["ef"], seed=1)
+
+
+def batch_graphs(count=512):
+    import graphgen
+    sizes = graphgen.chung_lu_batch_sizes(count, 10, 17, 1000)
+    return [graphgen.chung_lu(int(n), 12 * int(n), 2.3, max(2.0, int(n) / 4), seed=1000 + g)
+            for g, n in enumerate(sizes)]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def timed(fn, dev):
+    """CUDA-event time (ms) of fn() on the current stream."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def emit(args, metric, value, unit, ms_step, config, extra, world=1):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_secondary(args):
+    """The batching and differentiation workloads (same JSON contract)."""
+    import torch
+    import graphgen
+    import paper_1103_2405_gb300 as spg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    like = torch.empty(0, device=dev)
+    pk = peaks()
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    w = WORKLOADS[args.workload]
+    L0 = spg.launch_count()
+    if args.workload == "rwr64":
+        rp, col = graph(args.workload)
+        n, nnz = int(rp.shape[0] - 1), int(rp[-1])
+        seeds = graphgen.pick_seeds(rp, 64, 4)
+        f = spg.Format(rp, col, kind="pagerank", vec_width=64)
+        f.rwr(seeds, 0.15, tol=0.0, max_iter=args.warmup, like=like)
+        L0 = spg.launch_count()
+        with Clocks(0) as clk:
+            t = timed(lambda: f.rwr(seeds, 0.15, tol=0.0, max_iter=args.steps, like=like), dev)
+        ms = t / args.steps
+        alg = 8 * nnz + 2 * 4 * 64 * n + 4 * n
+        flops = 2.0 * nnz * 64
+        info = f.info()
+        cfg = {"workload": w["desc"], "n": n, "nnz": nnz, "k": 64, "parts": info["ntile"] + 1,
+               "tile_width": info["tile_width"], "l2": "inputs larger than L2"}
+        hs = torch.zeros(n, 64).pin_memory()
+        t1 = time.perf_counter()
+        for _ in range(3):
+            R, _ = f.rwr(seeds, 0.15, tol=0.0, max_iter=1, out=hs)
+        e2e_v = flops * 3 / (time.perf_counter() - t1) / 1e9
+        extra = {"roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
+                              "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                              "traffic": None, "kernel": "k_part_spmm<EPI_RWR> + check per iteration"},
+                 "e2e": {"value": e2e_v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                         "d2h_bytes_per_step": 4 * 64 * n}}
+        value = flops / (ms * 1e-3) / 1e9
+    elif args.workload == "batch512":
+        graphs = batch_graphs(512)
+        nnz = sum(int(g[0][-1]) for g in graphs)
+        n = sum(int(g[0].shape[0] - 1) for g in graphs)
+        b = spg.BatchFormat(graphs)
+        b.pagerank(DAMPING, tol=0.0, max_iter=args.warmup, like=like)
+        L0 = spg.launch_count()
+        with Clocks(0) as clk:
+            t = timed(lambda: b.pagerank(DAMPING, tol=0.0, max_iter=args.steps, like=like), dev)
+        ms = t / args.steps
+        alg = 8 * nnz + 16 * n + 8 * n
+        value = 2.0 * nnz / (ms * 1e-3) / 1e9
+        conv = timed(lambda: b.pagerank(DAMPING, tol=1e-8, max_iter=1000, like=like), dev)
+        hout = torch.empty(n).pin_memory()
+        t1 = time.perf_counter()
+        _, infos = b.pagerank(DAMPING, tol=1e-8, max_iter=1000, out=hout)
+        e2e_s = time.perf_counter() - t1
+        its = sum(i["iters"] for i in infos) / len(infos)
+        cfg = {"workload": w["desc"], "graphs": 512, "n": n, "nnz": nnz,
+               "full_solve_ms_tol_1e-8": conv, "mean_iters": its}
+        extra = {"roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
+                              "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                              "traffic": None, "kernel": "batched iteration (SpMV + per-graph sums)"},
+                 "e2e": {"value": 2.0 * nnz * max(i["iters"] for i in infos) / e2e_s / 1e9,
+                         "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * n}}
+    else:  # adjoint20
+        rp, col = graph(args.workload)
+        n, nnz = int(rp.shape[0] - 1), int(rp[-1])
+        theta = torch.from_numpy(graphgen.normal(nnz, 7)).to(dev)
+        s = graphgen.pick_source(rp, 3)
+        f = spg.Format(rp, col, val=theta.cpu().numpy(), kind="weighted", build_transpose=True)
+        f.set_edge_logits(theta)
+        r, _ = f.rwr_weighted(s, 0.15, 1e-10, 5000, like=theta)
+        t_idx = torch.from_numpy(graphgen.pick_targets(rp, col, s, 1000, 5).astype(np.int64)).to(dev)
+        g = torch.zeros_like(r)
+        g[t_idx] = -1.0 / r[t_idx]
+        f.rwr_adjoint(s, r, g, 0.15, tol=0.0, max_iter=args.warmup)
+        L0 = spg.launch_count()
+        with Clocks(0) as clk:
+            t = timed(lambda: f.rwr_adjoint(s, r, g, 0.15, tol=0.0, max_iter=args.steps), dev)
+        ms = t / args.steps
+        alg = 8 * nnz + 16 * n
+        value = 2.0 * nnz / (ms * 1e-3) / 1e9
+        full = timed(lambda: (f.set_edge_logits(theta), f.rwr_weighted(s, 0.15, 1e-8, 5000, like=theta),
+                              f.rwr_adjoint(s, r, g, 0.15, 1e-8, 5000)), dev)
+        cfg = {"workload": w["desc"], "n": n, "nnz": nnz, "targets": 1000,
+               "forward_plus_gradient_ms_tol_1e-8": full}
+        extra = {"roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
+                              "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                              "traffic": None, "kernel": "k_part<EPI_ADJ> + check per iteration"},
+                 "e2e": None}
+    extra["gpu_launches"] = spg.launch_count() - L0
+    extra["clocks"] = clk.summary()
+    extra["cpu_baseline"] = None
+    emit(args, "GFLOP/s (2*nnz per vector per iteration)", value, "GFLOP/s", ms, cfg, extra)
 
 
 def cpu_leg(rp, col, nnz, budget_s=12.0, max_iters=40):
@@ -136,6 +279,10 @@ def cpu_leg(rp, col, nnz, budget_s=12.0, max_iters=40):
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload in ("rwr64", "batch512", "adjoint20"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm times the "
+                          "PageRank workloads only"}), flush=True)
         return
     rp, col = graph(args.workload)
     nnz = int(rp[-1])
@@ -163,6 +310,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("rwr64", "batch512", "adjoint20"):
+        return run_secondary(args)
     import torch
     import paper_1103_2405_gb300 as spg
     rank, world, local = dist_env()

@@ -41,6 +41,8 @@ def _stale(objs) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    """Compile and link libspg.so; SPG_NVCC_FLAGS (environment) adds nvcc flags."""
+    extra_flags = tuple(extra_flags) + tuple(os.environ.get("SPG_NVCC_FLAGS", "").split())
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     objs = [os.path.join(BUILD, os.path.splitext(s)[0] + ".o") for s in SOURCES]

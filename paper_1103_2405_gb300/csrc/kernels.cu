@@ -28,7 +28,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // Resident blocks per SM the SpMV kernel is compiled for (8 x 8 warps = the
 // SM's 64-warp limit): the gather is latency bound, so occupancy is what
 // keeps enough loads in flight.
-constexpr int kPartMinBlocks = 6;
+#ifndef SPG_PART_MINB
+#define SPG_PART_MINB 6
+#endif
+constexpr int kPartMinBlocks = SPG_PART_MINB;
 // Staged variant: one 32-warp block per SM sharing up to kStagedMaxCols
 // floats (192 KB) of x in shared memory.
 constexpr int kStagedBlock = 1024;
