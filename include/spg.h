@@ -137,7 +137,7 @@ typedef struct {
     /* Most rows one workload may hold (not in the paper; GB300): a warp
      * walks its workload's 32-row blocks in sequence, so a tall workload of
      * one-entry rows is a long serial chain of dependent loads.  The
-     * Algorithm 3 model sees the capped rectangles.  0 = auto (64),
+     * Algorithm 3 model sees the capped rectangles.  0 = auto (32),
      * < 0 = no cap (the paper's packing). */
     int64_t max_rows;
 } spg_build_opts;

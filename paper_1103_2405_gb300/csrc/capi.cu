@@ -24,7 +24,7 @@
 using namespace spg;
 
 // Default cap on the rows of one workload (spg_build_opts.max_rows = 0).
-static constexpr int64_t kDefaultMaxRows = 64;
+static constexpr int64_t kDefaultMaxRows = 32;
 
 static thread_local std::string g_err;
 
