@@ -333,6 +333,36 @@ spg_status spg_baseline_spmv(spg_handle h, spg_baseline which, const float *x, f
 spg_status spg_baseline_pagerank(spg_handle h, spg_baseline which, float damping, double tol,
                                  int max_iter, float *p_out, spg_iter_info *info, void *stream);
 
+/* ----------------------------------------------- allocation-free SpMV -- */
+
+/* The paper has no counterpart to this entry point.
+ *
+ * Same product as spg_spmv_permuted (y' = M' x', device vectors in the
+ * handle's permuted order), for callers that must not allocate device
+ * memory during the call: a serving or real-time loop that reserved all of
+ * its device memory up front, a process whose device memory belongs to an
+ * allocator or pool it may not bypass, or one already at its memory limit,
+ * where a cudaMalloc can fail or stall the device.  This call allocates
+ * nothing (no cudaMalloc, no cudaFree, no allocating library routine):
+ * the scratch its kernels need -- partial sums and arrival counters of rows
+ * cut into chunks, work counters of the shared-memory kernel -- lives in one
+ * fixed array of 1,311,744 bytes inside the library, which every GPU that
+ * loads the library holds until the process exits.
+ *
+ *  - Limits: formats with at most 128 parts, 65,536 split rows and 262,144
+ *    split chunks (spg_format_info: ntile + 1, split_rows, split_chunks);
+ *    larger ones get SPG_ERR_INVALID with a message naming the limits.
+ *  - The handle's device must be the current device.  The first call on a
+ *    device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call on a device shares the one array and it keeps the last
+ *    call's contents: the call clears its counters on `stream` before its
+ *    kernels, but calls whose work overlaps on the GPU (other streams,
+ *    other threads) race on the array.  Order them on one stream.
+ *  - The handle itself is built (and allocates) beforehand, once. */
+spg_status spg_spmv_permuted_noalloc(spg_handle h, const float *x_perm, float *y_perm,
+                                     void *stream);
+
 /* -------------------------------------------------------------- misc -- */
 
 /* Load a performance table (Section 3.3 lookup table) for the process: text

@@ -75,7 +75,7 @@ EXPORTS = ["spg_build_format", "spg_destroy", "spg_format_info", "spg_tile_info"
            "spg_set_edge_logits", "spg_rwr_weighted", "spg_rwr_adjoint", "spg_build_batch",
            "spg_batch_offsets", "spg_batch_pagerank",
            "spg_baseline_spmv", "spg_baseline_pagerank", "spg_time_parts", "spg_load_table", "spg_launch_count",
-           "spg_status_string", "spg_last_error", "spg_version"]
+           "spg_status_string", "spg_last_error", "spg_version", "spg_spmv_permuted_noalloc"]
 
 _lib = None
 
@@ -113,6 +113,7 @@ def lib():
             "spg_baseline_spmv": [P, i32, P, P, f32, f32, P],
             "spg_baseline_pagerank": [P, i32, f32, f64, i32, P, ctypes.POINTER(IterInfo), P],
             "spg_time_parts": [P, i32, i32, P, P],
+            "spg_spmv_permuted_noalloc": [P, P, P, P],
             "spg_load_table": [ctypes.c_char_p],
         }
         for name, args in sig.items():

@@ -12,6 +12,7 @@
 #include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1117,6 +1118,101 @@ extern "C" spg_status spg_time_parts(spg_handle h, int mode, int reps, float *ms
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
         ms_out[p] = ms / (float)reps;
+    }
+    CK(cudaGetLastError());
+    return SPG_OK;
+}
+
+// ------------------------------------------------- allocation-free SpMV --
+//
+// spg_spmv_permuted_noalloc runs the same tiled-composite SpMV launches as
+// spg_spmv_permuted, but every piece of scratch those kernels need -- the
+// partial sums and arrival counters of rows cut into chunks, and the work
+// counters of the persistent shared-memory kernel -- comes from the fixed
+// array below instead of from device memory the handle allocated.  The
+// array is part of the library image: every GPU that loads the library
+// holds it (kNoAllocBytes) until the process exits.
+
+static constexpr int64_t kNoAllocMaxParts = 128;        // tiles + sparse part
+static constexpr int64_t kNoAllocMaxSplitRows = 65536;  // rows cut into chunks
+static constexpr int64_t kNoAllocMaxChunks = 262144;    // chunks of those rows
+static constexpr int64_t kNoAllocSchedWords = 2 * kNoAllocMaxParts;
+static constexpr size_t kNoAllocBytes =
+    (size_t)(kNoAllocSchedWords + kNoAllocMaxSplitRows + kNoAllocMaxChunks) * 4;  // 1.25 MiB + 1 KiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Host code cannot use g_noalloc_scratch as a device address: its device
+// address is looked up once per device, with that device current.
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[256];
+
+static spg_status noalloc_scratch_address(int dev, unsigned char **out)
+{
+    if (dev < 0 || dev >= 256) return fail(SPG_ERR_INVALID, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_spmv_permuted_noalloc(spg_handle h, const float *x_perm, float *y_perm,
+                                                void *stream)
+{
+    if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
+    if (!x_perm || !y_perm || x_perm == y_perm)
+        return fail(SPG_ERR_INVALID, "x and y must be distinct device vectors");
+    const Layout &L = h->fwd;
+    if ((int64_t)L.parts.size() > kNoAllocMaxParts || L.nsplit > kNoAllocMaxSplitRows ||
+        L.nchunk_slots > kNoAllocMaxChunks)
+        return fail(SPG_ERR_INVALID,
+                    "format too large for the fixed no-alloc scratch (at most 128 parts, 65536 "
+                    "split rows, 262144 split chunks; this format has " +
+                    std::to_string(L.parts.size()) + " parts, " + std::to_string(L.nsplit) +
+                    " split rows, " + std::to_string(L.nchunk_slots) +
+                    " chunks): use spg_spmv_permuted");
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != h->device) return fail(SPG_ERR_INVALID, "the handle's device must be current");
+    unsigned char *base = nullptr;
+    spg_status st = noalloc_scratch_address(cur, &base);
+    if (st != SPG_OK) return st;
+    uint32_t *sched = reinterpret_cast<uint32_t *>(base);
+    uint32_t *counter = sched + kNoAllocSchedWords;
+    float *partial = reinterpret_cast<float *>(counter + kNoAllocMaxSplitRows);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the work counters and arrival counters must start at zero; the array
+    // keeps whatever the previous call left in it
+    CK(cudaMemsetAsync(sched, 0, (size_t)(2 * L.parts.size()) * sizeof(uint32_t), s));
+    if (L.nsplit > 0) CK(cudaMemsetAsync(counter, 0, (size_t)L.nsplit * sizeof(uint32_t), s));
+    SplitView sv = L.split_view();
+    sv.partial = partial;
+    sv.counter = counter;
+    for (size_t p = 0; p < L.parts.size(); ++p) {
+        const PartHost &ph = L.parts[p];
+        PartView pv;
+        std::memset(&pv, 0, sizeof pv);
+        pv.wl = L.d_wl + ph.wl_off;
+        pv.rows = L.d_rows;
+        pv.slab = L.d_slab;
+        pv.sched = sched + 2 * p;
+        pv.nwl = (int32_t)ph.nwl_total;
+        pv.c0 = (int32_t)ph.c0;
+        pv.pf_ahead = h->pf_ahead;
+        const int64_t width = ph.c1 - ph.c0;
+        if (h->stage_cols > 0 && width >= 1024 && ph.nwl_total > 0) {
+            pv.xs_cols = (int32_t)std::min<int64_t>(h->stage_cols, width);
+            pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
+        } else {
+            pv.xs_cols = 0;
+            pv.nblocks = (int32_t)((ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        }
+        launch_part(EPI_RAW, pv, sv, x_perm, y_perm, nullptr, nullptr, s);
     }
     CK(cudaGetLastError());
     return SPG_OK;
