@@ -61,6 +61,19 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def aggregate_ranks(t_ms, units_per_rank, world, device=None):
+    """Replicas: every rank solves its own copy of the workload.  Whole-job
+    throughput = units of all ranks / the slowest rank's time (max over ranks,
+    by all-reduce when world > 1).  Returns (t_max_ms, units_per_second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    return t_ms, units_per_rank * world / (t_ms * 1e-3)
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -343,13 +356,9 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     launches = spg.launch_count() - L0
-    t_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms, flops_per_s = aggregate_ranks(ev0.elapsed_time(ev1), 2.0 * nnz * args.steps, world, dev)
     ms_step = t_ms / args.steps
-    value = 2.0 * nnz * args.steps * world / (t_ms * 1e-3) / 1e9
+    value = flops_per_s / 1e9
 
     # ---- dominant kernel: the fused PageRank tiled-composite kernel, alone
     part_ms = f.time_parts(mode=1, reps=max(20, args.steps // 2))

@@ -68,6 +68,7 @@ struct Epi {
     const float *aux;
     const int32_t *gid;
     const float *gbase;
+    float xs;            // adjoint: x[seed] of the current launch
 };
 
 template <int MODE>
@@ -76,6 +77,7 @@ __device__ __forceinline__ Epi load_epi(const IterState *st)
     Epi E;
     E.c = 1.f; E.base = 0.f; E.tele = 0.f; E.seed = -1; E.dstart = 0;
     E.sc[0] = E.sc[1] = 1.f; E.hnorm = 2; E.aux = nullptr; E.gid = nullptr; E.gbase = nullptr;
+    E.xs = 0.f;
     if (MODE == EPI_BATCH) {
         E.c = (float)st->c;
         E.gid = st->gid;
@@ -165,6 +167,87 @@ __device__ __forceinline__ void finish_row(const Epi &E, const SplitView &sv, do
     else epilogue<MODE>(E, rid, acc, x, y, r0, r1);
 }
 
+// What a row's epilogue reads besides its sum, fetched before the sum is
+// computed so the loads overlap the slot stream: the row entry, y_v (rows
+// continued from an earlier part), x_v (the L1 change), and the per-row
+// additive term of the adjoint / batch epilogues.
+struct RowPre {
+    uint32_t rid;
+    float yv, xv, av;
+};
+
+template <int MODE>
+__device__ __forceinline__ RowPre prefetch_row(const Epi &E, const uint32_t *__restrict__ rows,
+                                               int i, bool valid, const float *__restrict__ x,
+                                               const float *__restrict__ y)
+{
+    RowPre p{0u, 0.f, 0.f, 0.f};
+    if (!valid) return p;
+    p.rid = __ldg(rows + i);
+    if (p.rid & kRowSplit) return p;
+    const uint32_t v = p.rid & kRowIdMask;
+    if (p.rid & kRowNotFirst) p.yv = y[v];
+    if (!(p.rid & kRowNotLast)) {
+        if (MODE == EPI_PAGERANK || MODE == EPI_RWR || MODE == EPI_ADJ) p.xv = x[v];
+        if (MODE == EPI_ADJ) p.av = __ldg(E.aux + v);
+        if (MODE == EPI_BATCH) p.av = __ldg(E.gbase + __ldg(E.gid + v));
+    }
+    return p;
+}
+
+__device__ __forceinline__ RowPre shfl_row(const RowPre &p, int src)
+{
+    RowPre q;
+    q.rid = __shfl_sync(kFull, p.rid, src);
+    q.yv = __shfl_sync(kFull, p.yv, src);
+    q.xv = __shfl_sync(kFull, p.xv, src);
+    q.av = __shfl_sync(kFull, p.av, src);
+    return q;
+}
+
+// The epilogue of a row whose extra operands were prefetched (same
+// arithmetic as epilogue()).
+template <int MODE>
+__device__ __forceinline__ void epilogue_pre(const Epi &E, const RowPre &p, float tot,
+                                             float *__restrict__ y, double &r0, double &r1)
+{
+    const uint32_t rid = p.rid, v = rid & kRowIdMask;
+    if (rid & kRowNotFirst) tot += p.yv;
+    if (rid & kRowNotLast) { y[v] = tot; return; }
+    if (MODE == EPI_RAW) {
+        y[v] = tot;
+    } else if (MODE == EPI_PAGERANK || MODE == EPI_RWR) {
+        float add = MODE == EPI_PAGERANK ? E.base : ((int)v == E.seed ? E.tele : 0.f);
+        float f = fmaf(E.c, tot, add);
+        y[v] = f;
+        r0 += fabs((double)f - (double)p.xv);
+        if ((int64_t)v >= E.dstart) r1 += (double)f;
+    } else if (MODE == EPI_BATCH) {
+        y[v] = fmaf(E.c, tot, p.av);
+    } else if (MODE == EPI_ADJ) {
+        const float add = (rid & kRowClass) ? E.c * E.xs : 0.f;
+        const float f = fmaf(E.c, tot, add + p.av);
+        y[v] = f;
+        r0 += fabs((double)f - (double)p.xv);
+    } else {
+        const int cls = (rid & kRowClass) ? 1 : 0;
+        float f = tot * (cls ? E.sc[0] : E.sc[1]);
+        y[v] = f;
+        double q = E.hnorm == 2 ? (double)f * (double)f : (double)f;
+        if (cls == 0) r0 += q; else r1 += q;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void finish_row_pre(const Epi &E, const SplitView &sv, double2 *red,
+                                               const RowPre &p, float acc,
+                                               const float *__restrict__ x, float *__restrict__ y,
+                                               double &r0, double &r1)
+{
+    if (p.rid & kRowSplit) finish_split<MODE>(E, sv, red, p.rid, acc, x, y);
+    else epilogue_pre<MODE>(E, p, acc, y, r0, r1);
+}
+
 template <int MODE>
 __device__ __forceinline__ void block_reduce_store(double r0, double r1, double2 *out)
 {
@@ -245,38 +328,54 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
                     (unsigned)pv.pf_ahead};
     if (pf.ahead) pf.advance(0u, lane);
     if (d.major == 0) {
-        // row-major (CSR-vector): the warp strides across one row at a time,
-        // 8 slots per lane in flight before their gathers
-        for (int i = 0; i < d.h; ++i) {
-            const uint2 *s = slab + (int64_t)i * d.w;
-            float acc = 0.f;
-            int e = lane;
-            for (; e + 224 < d.w; e += 256) {
-                if (pf.ahead) pf.advance((unsigned)(((int64_t)i * d.w + e - lane) * 8), lane);
-                uint2 a[8];
+        // row-major (CSR-vector): the warp strides across one row at a time;
+        // the next 4 slots per lane are in flight while the current 4 gather
+        const int nst = d.w >> 5;   // 32-slot steps per row
+        for (int g0 = 0; g0 < d.h; g0 += 32) {
+            const RowPre mine = prefetch_row<MODE>(E, rows, g0 + lane, g0 + lane < d.h, x, y);
+            const int gend = min(d.h, g0 + 32);
+            for (int i = g0; i < gend; ++i) {
+                const uint2 *s = slab + (int64_t)i * d.w + lane;
+                float acc = 0.f;
+                int st = 0;
+                if (nst >= 4) {
+                    uint2 a0 = __ldcs(s), a1 = __ldcs(s + 32), a2 = __ldcs(s + 64), a3 = __ldcs(s + 96);
+                    for (st = 4; st + 4 <= nst; st += 4) {
+                        if (pf.ahead) pf.advance((unsigned)(((int64_t)i * d.w + st * 32) * 8), lane);
+                        const uint2 *q = s + st * 32;
+                        const uint2 b0 = __ldcs(q), b1 = __ldcs(q + 32), b2 = __ldcs(q + 64), b3 = __ldcs(q + 96);
+                        acc = slot_fma_g(a0, g, acc);
+                        acc = slot_fma_g(a1, g, acc);
+                        acc = slot_fma_g(a2, g, acc);
+                        acc = slot_fma_g(a3, g, acc);
+                        a0 = b0; a1 = b1; a2 = b2; a3 = b3;
+                    }
+                    acc = slot_fma_g(a0, g, acc);
+                    acc = slot_fma_g(a1, g, acc);
+                    acc = slot_fma_g(a2, g, acc);
+                    acc = slot_fma_g(a3, g, acc);
+                }
+                {   // the last < 4 steps (all of a short row): loads first
+                    uint2 r[3];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) a[u] = __ldcs(s + e + 32 * u);
+                    for (int u = 0; u < 3; ++u)
+                        r[u] = st + u < nst ? __ldcs(s + (st + u) * 32) : make_uint2(0xffffffffu, 0u);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc = slot_fma_g(a[u], g, acc);
+                    for (int u = 0; u < 3; ++u) acc = slot_fma_g(r[u], g, acc);
+                }
+                acc = warp_sum(acc);
+                const RowPre p = shfl_row(mine, i - g0);
+                if (lane == 0) finish_row_pre<MODE>(E, sv, red, p, acc, x, y, r0, r1);
+                if (pf.ahead) pf.advance((unsigned)((int64_t)(i + 1) * d.w * 8), lane);
             }
-            if (e + 96 < d.w) {
-                uint2 a[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) a[u] = __ldcs(s + e + 32 * u);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc = slot_fma_g(a[u], g, acc);
-                e += 128;
-            }
-            for (; e < d.w; e += 32) acc = slot_fma_g(__ldcs(s + e), g, acc);
-            acc = warp_sum(acc);
-            if (lane == 0) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc, x, y, r0, r1);
-            if (pf.ahead) pf.advance((unsigned)((int64_t)(i + 1) * d.w * 8), lane);
         }
     } else {
         // column-major (ELL): one row per lane; two 32-row blocks per pass so
         // each lane keeps two independent load chains in flight
         for (int b = 0; b < hp; b += 64) {
             const bool two = b + 32 < hp;
+            const RowPre pa = prefetch_row<MODE>(E, rows, b + lane, b + lane < d.h, x, y);
+            const RowPre pb = prefetch_row<MODE>(E, rows, b + 32 + lane, two && b + 32 + lane < d.h, x, y);
             const uint2 *sa = slab + (int64_t)b * d.w + lane;
             const uint2 *sb = sa + (int64_t)32 * d.w;
             float acc_a = 0.f, acc_b = 0.f;
@@ -310,14 +409,17 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
 #pragma unroll
                     for (int u = 0; u < 8; ++u) acc_a = slot_fma_g(a[u], g, acc_a);
                 }
-                for (; e < d.w; ++e) acc_a = slot_fma_g(__ldcs(sa + (int64_t)e * 32), g, acc_a);
+                {
+                    uint2 r[7];
+#pragma unroll
+                    for (int u = 0; u < 7; ++u)
+                        r[u] = e + u < d.w ? __ldcs(sa + (int64_t)(e + u) * 32) : make_uint2(0xffffffffu, 0u);
+#pragma unroll
+                    for (int u = 0; u < 7; ++u) acc_a = slot_fma_g(r[u], g, acc_a);
+                }
             }
-            int i = b + lane;
-            if (i < d.h) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc_a, x, y, r0, r1);
-            if (two) {
-                i += 32;
-                if (i < d.h) finish_row<MODE>(E, sv, red, __ldg(rows + i), acc_b, x, y, r0, r1);
-            }
+            if (b + lane < d.h) finish_row_pre<MODE>(E, sv, red, pa, acc_a, x, y, r0, r1);
+            if (two && b + 32 + lane < d.h) finish_row_pre<MODE>(E, sv, red, pb, acc_b, x, y, r0, r1);
             if (pf.ahead) pf.advance((unsigned)((int64_t)(b + 64) * d.w * 8), lane);
         }
     }
@@ -342,8 +444,9 @@ k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restri
 {
     const float *x = xin;
     float *y = yout;
-    const Epi E = load_epi<MODE>(st);
+    Epi E = load_epi<MODE>(st);
     resolve_xy<MODE>(st, x, y);
+    if (MODE == EPI_ADJ) E.xs = x[E.seed];
     const int lane = threadIdx.x & 31;
     const int wid = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     double r0 = 0.0, r1 = 0.0;
@@ -369,8 +472,9 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
     extern __shared__ float xs[];
     const float *x = xin;
     float *y = yout;
-    const Epi E = load_epi<MODE>(st);
+    Epi E = load_epi<MODE>(st);
     resolve_xy<MODE>(st, x, y);
+    if (MODE == EPI_ADJ) E.xs = x[E.seed];
     const int S = pv.xs_cols, c0 = pv.c0;
     if (((c0 | S) & 3) == 0) {
         const float4 *src = reinterpret_cast<const float4 *>(x + c0);
@@ -642,12 +746,157 @@ k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__r
     }
 }
 
+// k = 64 specialisation: one row per half-warp (16 lanes x float4 = the 64
+// columns), so a warp keeps two rows and, per lane, four 256-byte X-row
+// gathers in flight.  Entries are fetched 16 at a time (one per lane of the
+// half) and broadcast within the half.  Same layout, split-row handling and
+// per-column sums as k_part_spmm.
+template <int MODE>
+__device__ __forceinline__ void epilogue_k64(float c, int64_t dstart, uint32_t rid, float4 t,
+                                             int j0, const float *__restrict__ X,
+                                             float *__restrict__ Y, const int32_t *seeds,
+                                             const double *delta_k, double *acc8)
+{
+    const uint32_t v = rid & kRowIdMask;
+    float4 *yr = reinterpret_cast<float4 *>(Y + (int64_t)v * 64 + j0);
+    if (rid & kRowNotFirst) {
+        const float4 o = *yr;
+        t.x += o.x; t.y += o.y; t.z += o.z; t.w += o.w;
+    }
+    if ((rid & kRowNotLast) || MODE == EPI_RAW) { *yr = t; return; }
+    const float4 xo = *reinterpret_cast<const float4 *>(X + (int64_t)v * 64 + j0);
+    float tt[4] = {t.x, t.y, t.z, t.w}, xx[4] = {xo.x, xo.y, xo.z, xo.w}, f[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + q;
+        const float add = (int)v == __ldg(seeds + j) ? (float)((double)c * delta_k[j] + (1.0 - (double)c)) : 0.f;
+        f[q] = fmaf(c, tt[q], add);
+        acc8[q] += fabs((double)f[q] - (double)xx[q]);
+        if ((int64_t)v >= dstart) acc8[4 + q] += (double)f[q];
+    }
+    *yr = make_float4(f[0], f[1], f[2], f[3]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_part_spmm64(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__restrict__ Yout,
+              const IterState *__restrict__ st, const int32_t *__restrict__ seeds,
+              const double *__restrict__ delta_k, double *__restrict__ redk)
+{
+    const float *X = Xin;
+    float *Y = Yout;
+    float c = 1.f;
+    int64_t dstart = 0;
+    if (st) {
+        const int par = st->parity;
+        X = st->buf[par];
+        Y = st->buf[par ^ 1];
+        c = (float)st->c;
+        dstart = st->dangling_start;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = lane >> 4, hl = lane & 15;
+    const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
+    const int j0 = 4 * hl;
+    const int wid = blockIdx.x * kWarpsPerBlock + warp;
+    double acc8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (wid < pv.nwl) {
+        const Workload d = pv.wl[wid];
+        const uint2 *slab = pv.slab + d.slab;
+        for (int i0 = 0; i0 < d.h; i0 += 2) {
+            const int i = i0 + half;
+            const bool has = i < d.h;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int e0 = 0; e0 < d.w; e0 += 16) {
+                uint2 ent = make_uint2(0xffffffffu, 0u);
+                if (has && e0 + hl < d.w) ent = ld_entry(slab, d, i, e0 + hl);
+                const unsigned vb = __ballot_sync(kFull, (int)ent.x >= 0);
+                const int mine = __popc(vb & hmask);
+                const int tmax = max(mine, __shfl_xor_sync(kFull, mine, 16));
+                for (int t = 0; t < tmax; t += 4) {
+                    float4 xv[4];
+                    float vv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int cu = __shfl_sync(kFull, (int)ent.x, t + u, 16);
+                        vv[u] = __shfl_sync(kFull, __uint_as_float(ent.y), t + u, 16);
+                        xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (t + u < mine)
+                            xv[u] = __ldg(reinterpret_cast<const float4 *>(X + (int64_t)cu * 64 + j0));
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float w = t + u < mine ? vv[u] : 0.f;
+                        a.x = fmaf(w, xv[u].x, a.x); a.y = fmaf(w, xv[u].y, a.y);
+                        a.z = fmaf(w, xv[u].z, a.z); a.w = fmaf(w, xv[u].w, a.w);
+                    }
+                }
+                if (tmax < 16) break;
+            }
+            if (!has) continue;
+            const uint32_t rid = __ldg(pv.rows + d.rows + i);
+            if (rid & kRowSplit) {
+                const int slot = (int)(rid & 0x7fffffffu);
+                *reinterpret_cast<float4 *>(sv.partial + (int64_t)slot * 64 + j0) = a;
+                __threadfence();
+                __syncwarp(hmask);
+                const int s = sv.slot_owner[slot];
+                const SplitRow sr = sv.rows[s];
+                unsigned prev = 0;
+                if (hl == 0) prev = atomicAdd(sv.counter + s, 1u);
+                prev = __shfl_sync(hmask, prev, 0, 16);
+                if (prev != (unsigned)sr.nchunks - 1) continue;
+                __threadfence();
+                float4 tot = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int q = 0; q < sr.nchunks; ++q) {
+                    const float4 pq = __ldcg(reinterpret_cast<const float4 *>(
+                        sv.partial + (int64_t)(sr.first_slot + q) * 64 + j0));
+                    tot.x += pq.x; tot.y += pq.y; tot.z += pq.z; tot.w += pq.w;
+                }
+                double s8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                epilogue_k64<MODE>(c, dstart, sr.row, tot, j0, X, Y, seeds, delta_k, s8);
+                if (hl == 0) sv.counter[s] = 0u;
+                if (MODE != EPI_RAW) {
+                    double *o = redk + (int64_t)(sv.red_split_base + sr.red_slot) * 128;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { o[j0 + q] = s8[q]; o[64 + j0 + q] = s8[4 + q]; }
+                }
+            } else {
+                epilogue_k64<MODE>(c, dstart, rid, a, j0, X, Y, seeds, delta_k, acc8);
+            }
+        }
+    }
+    if (MODE != EPI_RAW) {
+        // both halves hold the same 4 columns: add them, then warps in order
+        __shared__ double sm[kWarpsPerBlock][16][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc8[q] += __shfl_xor_sync(kFull, acc8[q], 16);
+        if (half == 0) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sm[warp][hl][q] = acc8[q];
+        }
+        __syncthreads();
+        if (threadIdx.x < 128) {
+            const int qq = threadIdx.x >> 6, j = threadIdx.x & 63;   // qq 0: L1, 1: dangling
+            double acc = 0.0;
+            for (int w = 0; w < kWarpsPerBlock; ++w) acc += sm[w][j >> 2][qq * 4 + (j & 3)];
+            redk[(int64_t)(pv.red_base + blockIdx.x) * 128 + qq * 64 + j] = acc;
+        }
+    }
+}
+
 void launch_part_spmm(int mode, const PartView &pv, const SplitView &sv, const float *X, float *Y,
                       int k, const IterState *st, const int32_t *seeds, const double *delta_k,
                       double *redk, cudaStream_t s)
 {
     if (pv.nblocks <= 0) return;
     dim3 g(pv.nblocks), b(kBlock);
+    if (k == 64) {
+        if (mode == EPI_RAW) k_part_spmm64<EPI_RAW><<<g, b, 0, s>>>(pv, sv, X, Y, st, seeds, delta_k, redk);
+        else k_part_spmm64<EPI_RWR><<<g, b, 0, s>>>(pv, sv, X, Y, st, seeds, delta_k, redk);
+        count_launches(1);
+        return;
+    }
     const bool even = (k % 2) == 0;
     if (mode == EPI_RAW) {
         if (even) k_part_spmm<EPI_RAW, true><<<g, b, 0, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
