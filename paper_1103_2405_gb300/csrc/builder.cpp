@@ -712,6 +712,9 @@ std::vector<PartView> Layout::part_views() const
         pv.xs_cols = 0;
         pv.sched = nullptr;
         pv.pf_ahead = 0;
+        pv.status = nullptr;
+        pv.tma = 0;
+        pv.pad_ = 0;
         v.push_back(pv);
     }
     return v;

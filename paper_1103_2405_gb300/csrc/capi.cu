@@ -127,6 +127,8 @@ struct spg_format_t {
     } rt_fwd, rt_bwd;
     int64_t stage_cols = kStagedMaxCols;
     int32_t pf_ahead = 0;        // L2 bulk-prefetch distance of the slot stream (bytes, 0 = off)
+    int kernel = 0;              // 0: TMA-pipelined, 1: staged (register stream), 2: plain
+    uint32_t *d_status = nullptr;   // set by kernels whose bounded waits ran out
     int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
     int num_sms = 152;
     std::map<std::string, LoopGraph> graphs;
@@ -162,6 +164,7 @@ struct spg_format_t {
         cudaFree(d_rp); cudaFree(d_col); cudaFree(d_val); cudaFree(d_dangling);
         cudaFree(d_row_half); cudaFree(d_arp); cudaFree(d_acol); cudaFree(d_P);
         cudaFree(d_goff); cudaFree(d_gdstart); cudaFree(d_gid); cudaFree(d_giters);
+        cudaFree(d_status);
         cudaFree(d_gbase); cudaFree(d_gl1); cudaFree(d_gdelta);
         x.release(); y.release(); stage_in.release(); stage_out.release(); red.release();
         rt_fwd.sched.release();
@@ -301,6 +304,10 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     h->pf_ahead = o.slab_prefetch > 0 ? (int32_t)std::min<int64_t>(o.slab_prefetch, 1 << 20) : 0;
     h->pf_ahead = (h->pf_ahead + 255) / 256 * 256;
     h->loop_mode = o.loop_mode == 1 ? 1 : 0;
+    h->kernel = (o.kernel >= 0 && o.kernel <= 2) ? o.kernel : 0;
+    if (o.x_stage_cols < 0 && h->kernel == 0) h->kernel = 2;   // no shared-memory staging at all
+    CK(cudaMalloc((void **)&h->d_status, sizeof(uint32_t)));
+    CK(cudaMemset(h->d_status, 0, sizeof(uint32_t)));
     CK(h->rt_fwd.sched.ensure(2 * h->fwd.parts.size()));
     CK(cudaMemset(h->rt_fwd.sched.p, 0, 2 * h->fwd.parts.size() * sizeof(uint32_t)));
     CK(cudaMalloc((void **)&h->d_state, sizeof(IterState)));
@@ -619,7 +626,7 @@ extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, in
 static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
                                         spg_format_t::LayoutRT &rt, bool staged)
 {
-    staged = staged && h->stage_cols > 0 && rt.sched.p;
+    staged = staged && (h->stage_cols > 0 || h->kernel == 0) && h->kernel != 2 && rt.sched.p;
     spg_format_t::Views &V = staged ? rt.vstaged : rt.vplain;
     if (V.built) return V;
     int32_t base = 0;
@@ -635,8 +642,14 @@ static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
         pv.nwl = (int32_t)ph.nwl_total;
         pv.c0 = (int32_t)ph.c0;
         pv.pf_ahead = h->pf_ahead;
+        pv.status = h->d_status;
         const int64_t width = ph.c1 - ph.c0;
-        if (staged && width >= 1024 && ph.nwl_total > 0) {
+        if (staged && h->kernel == 0 && ph.nwl_total > 0) {
+            // TMA-pipelined persistent kernel (x slice when the part is wide enough)
+            pv.tma = 1;
+            pv.xs_cols = width >= 1024 ? (int32_t)std::min<int64_t>(kTmaMaxCols, width) : 0;
+            pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
+        } else if (staged && width >= 1024 && ph.nwl_total > 0) {
             pv.xs_cols = (int32_t)std::min<int64_t>(h->stage_cols, width);
             pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
         } else {
@@ -840,6 +853,17 @@ static IterState make_state(spg_handle h, double c, double tol, int max_iter, in
 }
 
 // Run the loop graph `g` (max_iter > 0) and read back the state.
+// Read and clear the kernels' status word (after the stream has synchronised).
+static spg_status take_status(spg_handle h)
+{
+    if (!h->d_status) return SPG_OK;
+    uint32_t st = 0;
+    CK(cudaMemcpy(&st, h->d_status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st == 0) return SPG_OK;
+    CK(cudaMemset(h->d_status, 0, sizeof st));
+    return fail(SPG_ERR_TIMEOUT, "a bounded wait on a TMA copy ran out in the SpMV kernel");
+}
+
 static spg_status run_loop(spg_handle h, LoopGraph *g, int max_iter, IterState *hs,
                            spg_iter_info *info, cudaStream_t s)
 {
@@ -863,6 +887,8 @@ static spg_status run_loop(spg_handle h, LoopGraph *g, int max_iter, IterState *
     }
     CK(cudaMemcpyAsync(hs, h->d_state, sizeof(IterState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    spg_status stw = take_status(h);
+    if (stw != SPG_OK) return stw;
     count_launches((int64_t)hs->iter * g->kernels_per_iter);
     if (info) {
         info->iters = hs->iter;
@@ -1120,7 +1146,7 @@ extern "C" spg_status spg_time_parts(spg_handle h, int mode, int reps, float *ms
         ms_out[p] = ms / (float)reps;
     }
     CK(cudaGetLastError());
-    return SPG_OK;
+    return take_status(h);
 }
 
 // ------------------------------------------------- allocation-free SpMV --

@@ -504,6 +504,221 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
     if (MODE != EPI_RAW && MODE != EPI_BATCH) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
 }
 
+// ------------------------------------------------ TMA-pipelined kernel --
+//
+// The slot stream is the one large sequential stream of the SpMV, and a
+// warp's workload occupies one contiguous, 256-byte aligned region of it
+// consumed front to back (row-major: row after row; column-major: 32-slot
+// columns of a 32-row block).  Each warp therefore streams its region into a
+// ring of kTmaStages shared-memory chunks with TMA bulk copies
+// (cp.async.bulk ... mbarrier::complete_tx): in-flight data holds no
+// registers, so every warp keeps 4 KB of slots in flight, and slots are read
+// from shared memory in batches of 4 steps whose x gathers are issued back
+// to back.  Lane 0 is the producer of its own warp's ring; every wait is
+// bounded and records a status flag instead of hanging.
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    uint64_t state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state) : "r"(smem_addr(bar)), "r"(bytes) : "memory");
+    (void)state;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_copy_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+constexpr int kTmaSteps = kTmaChunk / 256;        // 32-slot steps per chunk
+constexpr uint32_t kTmaWaitLimit = 1u << 22;      // try_wait rounds before giving up
+
+struct TmaRing {
+    char *buf;            // kTmaStages x kTmaChunk bytes of this warp
+    uint64_t *bar;        // kTmaStages barriers of this warp
+    uint32_t used;        // chunks this warp has consumed so far (all workloads)
+    bool fail;
+};
+
+// Issue chunk c of the region `src` (bytes total) into its stage.
+__device__ __forceinline__ void tma_issue(TmaRing &R, const char *src, uint32_t bytes, uint32_t c)
+{
+    const uint32_t k = R.used + c, st = k % kTmaStages;
+    const uint32_t n = min((uint32_t)kTmaChunk, bytes - c * kTmaChunk);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(R.bar + st, n);
+    tma_copy_1d(R.buf + st * kTmaChunk, src + (size_t)c * kTmaChunk, n, R.bar + st);
+}
+
+__device__ __forceinline__ bool tma_wait(TmaRing &R, uint32_t c)
+{
+    const uint32_t k = R.used + c, st = k % kTmaStages, parity = (k / kTmaStages) & 1u;
+    for (uint32_t it = 0; it < kTmaWaitLimit; ++it)
+        if (mbar_try_wait(R.bar + st, parity)) return true;
+    return false;
+}
+
+template <int MODE, class G>
+__device__ __forceinline__ void do_workload_tma(const Workload &d, const PartView &pv,
+                                                const SplitView &sv, const G &g, const Epi &E,
+                                                const float *__restrict__ x,
+                                                float *__restrict__ y, double2 *red, int lane,
+                                                TmaRing &R, double &r0, double &r1)
+{
+    const uint32_t *__restrict__ rows = pv.rows + d.rows;
+    const int hp = d.major == 0 ? d.h : (d.h + 31) & ~31;
+    const uint32_t bytes = (uint32_t)((int64_t)hp * d.w * 8);
+    const uint32_t nch = (bytes + kTmaChunk - 1) / kTmaChunk;
+    const char *src = reinterpret_cast<const char *>(pv.slab + d.slab);
+    if (lane == 0)
+        for (uint32_t c = 0; c < nch && c < (uint32_t)kTmaStages; ++c) tma_issue(R, src, bytes, c);
+    // steps per row (row-major) or per 32-row block (column-major)
+    const int per = d.major == 0 ? (d.w >> 5) : d.w;
+    int left = per;                // steps left in the current row / block
+    int unit = 0;                  // current row (row-major) or block (column-major)
+    RowPre mine = prefetch_row<MODE>(E, rows, lane, lane < d.h, x, y);
+    float acc = 0.f;
+    if (nch == 0) {                // rows without entries (w = 0)
+        for (int b = 0; b < hp; b += 32) {
+            if (b > 0) mine = prefetch_row<MODE>(E, rows, b + lane, b + lane < d.h, x, y);
+            if (b + lane < d.h) finish_row_pre<MODE>(E, sv, red, mine, 0.f, x, y, r0, r1);
+        }
+        return;
+    }
+    for (uint32_t c = 0; c < nch; ++c) {
+        if (!tma_wait(R, c)) {
+            // give up: record it, then let the copies still in flight land
+            // (each wait bounded again) before the warp leaves its ring
+            R.fail = true;
+            for (uint32_t q = c + 1; q < nch && q < c + kTmaStages; ++q) tma_wait(R, q);
+            break;
+        }
+        const uint32_t st = (R.used + c) % kTmaStages;
+        const uint2 *ch = reinterpret_cast<const uint2 *>(R.buf + st * kTmaChunk);
+        const int steps = (int)min((uint32_t)kTmaSteps, (bytes - c * kTmaChunk) / 256u);
+        uint2 sl[kTmaSteps];
+        float xv[kTmaSteps];
+#pragma unroll
+        for (int j = 0; j < kTmaSteps; ++j) sl[j] = j < steps ? ch[j * 32 + lane] : make_uint2(0xffffffffu, 0u);
+        __syncwarp();
+        if (lane == 0 && c + kTmaStages < nch) tma_issue(R, src, bytes, c + kTmaStages);
+#pragma unroll
+        for (int j = 0; j < kTmaSteps; ++j) xv[j] = (int)sl[j].x >= 0 ? g((int)sl[j].x) : 0.f;
+#pragma unroll
+        for (int j = 0; j < kTmaSteps; ++j) {
+            if (j >= steps) break;
+            acc = fmaf(__uint_as_float(sl[j].y), xv[j], acc);
+            if (--left > 0) continue;
+            left = per;
+            if (d.major == 0) {
+                const int i = unit++;
+                const float tot = warp_sum(acc);
+                if (i > 0 && (i & 31) == 0)
+                    mine = prefetch_row<MODE>(E, rows, i + lane, i + lane < d.h, x, y);
+                const RowPre p = shfl_row(mine, i & 31);
+                if (lane == 0) finish_row_pre<MODE>(E, sv, red, p, tot, x, y, r0, r1);
+            } else {
+                const int b = unit++ * 32;
+                if (b + lane < d.h) finish_row_pre<MODE>(E, sv, red, mine, acc, x, y, r0, r1);
+                if (b + 32 < hp) mine = prefetch_row<MODE>(E, rows, b + 32 + lane, b + 32 + lane < d.h, x, y);
+            }
+            acc = 0.f;
+        }
+    }
+    R.used += nch;
+}
+
+// One persistent 32-warp block per SM: x[c0, c0 + xs_cols) in shared memory
+// as in k_part_staged, plus the per-warp TMA rings.  Shared memory:
+// barriers (1 KB), rings (32 x 4 KB), x slice.
+template <int MODE>
+__global__ void __launch_bounds__(kStagedBlock, 1)
+k_part_tma(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restrict__ yout,
+           const IterState *__restrict__ st, double2 *__restrict__ red)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int kWarps = kStagedBlock / 32;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    char *ring = reinterpret_cast<char *>(smem + 1024);
+    float *xs = reinterpret_cast<float *>(smem + 1024 + kWarps * kTmaStages * kTmaChunk);
+    const float *x = xin;
+    float *y = yout;
+    Epi E = load_epi<MODE>(st);
+    resolve_xy<MODE>(st, x, y);
+    if (MODE == EPI_ADJ) E.xs = x[E.seed];
+    const int S = pv.xs_cols, c0 = pv.c0;
+    if (((c0 | S) & 3) == 0) {
+        const float4 *src4 = reinterpret_cast<const float4 *>(x + c0);
+        float4 *dst4 = reinterpret_cast<float4 *>(xs);
+        for (int i = threadIdx.x; i < (S >> 2); i += blockDim.x) dst4[i] = __ldg(src4 + i);
+    } else {
+        for (int i = threadIdx.x; i < S; i += blockDim.x) xs[i] = __ldg(x + c0 + i);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    TmaRing R{ring + warp * kTmaStages * kTmaChunk, bars + warp * kTmaStages, 0u, false};
+    if (lane == 0) {
+        for (int s2 = 0; s2 < kTmaStages; ++s2) mbar_init(R.bar + s2, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const GatherStaged g{x, xs, c0, (unsigned)S};
+    double r0 = 0.0, r1 = 0.0;
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(pv.sched, 1u);
+        w = __shfl_sync(kFull, w, 0);
+        if (w >= (unsigned)pv.nwl || R.fail) break;
+        do_workload_tma<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, R, r0, r1);
+    }
+    if (lane == 0) {
+        if (R.fail) atomicOr(pv.status, 1u);
+        const unsigned done = atomicAdd(pv.sched + 1, 1u);
+        if (done == gridDim.x * (blockDim.x >> 5) - 1) {   // every warp has left the loop
+            pv.sched[0] = 0u;
+            pv.sched[1] = 0u;
+        }
+    }
+    if (MODE != EPI_RAW && MODE != EPI_BATCH)
+        block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
+}
+
+constexpr size_t kTmaSmemFixed = 1024 + (size_t)(kStagedBlock / 32) * kTmaStages * kTmaChunk;
+
+template <int MODE> static void launch_tma(const PartView &pv, const SplitView &sv, const float *x,
+                                           float *y, const IterState *st, double2 *red,
+                                           cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_part_tma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kTmaSmemFixed + kTmaMaxCols * sizeof(float)));
+        attr = true;
+    }
+    k_part_tma<MODE><<<pv.nblocks, kStagedBlock, kTmaSmemFixed + (size_t)pv.xs_cols * sizeof(float), s>>>(
+        pv, sv, x, y, st, red);
+}
+
 int part_blocks_per_sm()
 {
     int b = 0;
@@ -530,6 +745,18 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
                  const IterState *st, double2 *red, cudaStream_t s)
 {
     if (pv.nblocks <= 0) return;
+    if (pv.tma) {
+        switch (mode) {
+        case EPI_RAW: launch_tma<EPI_RAW>(pv, sv, x, y, st, red, s); break;
+        case EPI_PAGERANK: launch_tma<EPI_PAGERANK>(pv, sv, x, y, st, red, s); break;
+        case EPI_RWR: launch_tma<EPI_RWR>(pv, sv, x, y, st, red, s); break;
+        case EPI_ADJ: launch_tma<EPI_ADJ>(pv, sv, x, y, st, red, s); break;
+        case EPI_BATCH: launch_tma<EPI_BATCH>(pv, sv, x, y, st, red, s); break;
+        default: launch_tma<EPI_HITS>(pv, sv, x, y, st, red, s); break;
+        }
+        count_launches(1);
+        return;
+    }
     if (pv.xs_cols > 0) {
         switch (mode) {
         case EPI_RAW: launch_staged<EPI_RAW>(pv, sv, x, y, st, red, s); break;

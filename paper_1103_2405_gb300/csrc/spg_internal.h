@@ -54,13 +54,22 @@ struct PartView {
     const uint32_t *rows;
     const uint2 *slab;
     uint32_t *sched;      // staged kernel: {next workload, warps done}, zero between launches
+    uint32_t *status;     // TMA kernel: set non-zero when a bounded wait ran out
     int32_t nwl;          // workloads incl. zero-row ones
     int32_t nblocks;      // launch blocks
     int32_t red_base;     // first reduction slot of this part's blocks
     int32_t c0;           // first column of the part
     int32_t xs_cols;      // > 0: columns [c0, c0 + xs_cols) staged in shared memory
     int32_t pf_ahead;     // bytes of a workload's slots prefetched into L2 ahead of use (0 = off)
+    int32_t tma;          // 1: slots streamed into shared memory by TMA bulk copies
+    int32_t pad_;
 };
+
+// TMA-pipelined kernel: per warp a ring of kTmaStages chunks of kTmaChunk
+// bytes (128 slots), and at most kTmaMaxCols floats of x in shared memory.
+constexpr int kTmaChunk = 1024;
+constexpr int kTmaStages = 4;
+constexpr int kTmaMaxCols = 24576;
 
 // Largest x slice staged in shared memory (floats): 192 KB.
 constexpr int kStagedMaxCols = 49152;

@@ -21,6 +21,8 @@ import numpy as np
 
 N_COLS = 1 << 22
 TARGET_NNZ = 1 << 24
+MAX_NNZ = 1 << 27
+MAX_WL = 1 << 15          # the paper's bound on the workload size of the table
 
 
 def shapes():
@@ -30,21 +32,25 @@ def shapes():
     out = []
     for lw in range(5, 14):
         for lh in range(0, 6):
-            out.append((0, 1 << lw, 1 << lh))
+            if (1 << (lw + lh)) <= MAX_WL:
+                out.append((0, 1 << lw, 1 << lh))
     for lw in range(0, 5):
         for lh in (5, 6):
             out.append((1, 1 << lw, 1 << lh))
     return out
 
 
-def shape_matrix(w, h, rng):
-    """CSR with R = TARGET_NNZ / w rows of exactly w entries (random distinct
-    columns), the remaining rows empty; square N_COLS x N_COLS."""
-    rows = max(h, min(N_COLS, TARGET_NNZ // w))
+def shape_matrix(w, h, rng, max_warps):
+    """Enough workloads of the shape to fill the GPU twice over (at
+    least TARGET_NNZ slots, at most MAX_NNZ): R rows of exactly w entries
+    with random columns over N_COLS (or R) columns, any other rows empty."""
+    slots = min(MAX_NNZ, max(TARGET_NNZ, 2 * max_warps * w * h))
+    rows = max(h, slots // w)
     rows -= rows % h
-    cols = rng.integers(0, N_COLS, size=(rows, w), dtype=np.int64)
+    n = max(N_COLS, rows)
+    cols = rng.integers(0, n, size=(rows, w), dtype=np.int64)
     cols.sort(axis=1)
-    rowptr = np.zeros(N_COLS + 1, np.int64)
+    rowptr = np.zeros(n + 1, np.int64)
     rowptr[1:rows + 1] = np.arange(1, rows + 1) * w
     rowptr[rows + 1:] = rows * w
     vals = rng.random(rows * w, dtype=np.float32)
@@ -63,12 +69,14 @@ def measure(out_path, reps=20, seed=0):
     del empty
     lines = ["# spg performance table: major log2(w_pad) log2(h_pad) slots_per_second",
              f"# measured {time.strftime('%Y-%m-%d %H:%M:%S')} on {torch.cuda.get_device_name(0)}"]
+    max_warps = torch.cuda.get_device_properties(0).multi_processor_count * 32
     for major, w, h in shapes():
-        rowptr, col, val, rows = shape_matrix(w, h, rng)
+        rowptr, col, val, rows = shape_matrix(w, h, rng, max_warps)
+        n = rowptr.shape[0] - 1
         f = spg.Format(rowptr, col, val, kind="matrix", tile_width=-1, wl=w * h, max_rows=h,
                        heavy_row=0, layout_rule=0, table=None)
         ms = float(f.time_parts(mode=0, reps=reps).sum())
-        ms_work = max(ms - t_empty * (N_COLS - rows) / N_COLS, 0.05 * ms)
+        ms_work = max(ms - t_empty * (n - rows) / N_COLS, 0.05 * ms)
         slots = rows * w
         perf = slots / (ms_work * 1e-3)
         lines.append(f"{major} {int(np.log2(w))} {int(np.log2(h))} {perf:.6e}")
