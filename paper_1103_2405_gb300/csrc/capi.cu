@@ -127,7 +127,7 @@ struct spg_format_t {
     } rt_fwd, rt_bwd;
     int64_t stage_cols = kStagedMaxCols;
     int32_t pf_ahead = 0;        // L2 bulk-prefetch distance of the slot stream (bytes, 0 = off)
-    int kernel = 0;              // 0: TMA-pipelined, 1: staged (register stream), 2: plain
+    int kernel = 0;              // 0/1: register stream + staged x slice, 2: plain, 3: TMA ring
     uint32_t *d_status = nullptr;   // set by kernels whose bounded waits ran out
     int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
     int num_sms = 152;
@@ -304,8 +304,8 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     h->pf_ahead = o.slab_prefetch > 0 ? (int32_t)std::min<int64_t>(o.slab_prefetch, 1 << 20) : 0;
     h->pf_ahead = (h->pf_ahead + 255) / 256 * 256;
     h->loop_mode = o.loop_mode == 1 ? 1 : 0;
-    h->kernel = (o.kernel >= 0 && o.kernel <= 2) ? o.kernel : 0;
-    if (o.x_stage_cols < 0 && h->kernel == 0) h->kernel = 2;   // no shared-memory staging at all
+    h->kernel = (o.kernel >= 0 && o.kernel <= 3) ? o.kernel : 0;
+    if (o.x_stage_cols < 0 && h->kernel <= 1) h->kernel = 2;   // no shared-memory staging at all
     CK(cudaMalloc((void **)&h->d_status, sizeof(uint32_t)));
     CK(cudaMemset(h->d_status, 0, sizeof(uint32_t)));
     CK(h->rt_fwd.sched.ensure(2 * h->fwd.parts.size()));
@@ -626,7 +626,7 @@ extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, in
 static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
                                         spg_format_t::LayoutRT &rt, bool staged)
 {
-    staged = staged && (h->stage_cols > 0 || h->kernel == 0) && h->kernel != 2 && rt.sched.p;
+    staged = staged && (h->stage_cols > 0 || h->kernel == 3) && h->kernel != 2 && rt.sched.p;
     spg_format_t::Views &V = staged ? rt.vstaged : rt.vplain;
     if (V.built) return V;
     int32_t base = 0;
@@ -644,7 +644,7 @@ static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
         pv.pf_ahead = h->pf_ahead;
         pv.status = h->d_status;
         const int64_t width = ph.c1 - ph.c0;
-        if (staged && h->kernel == 0 && ph.nwl_total > 0) {
+        if (staged && h->kernel == 3 && ph.nwl_total > 0) {
             // TMA-pipelined persistent kernel (x slice when the part is wide enough)
             pv.tma = 1;
             pv.xs_cols = width >= 1024 ? (int32_t)std::min<int64_t>(kTmaMaxCols, width) : 0;

@@ -487,18 +487,12 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
     const GatherStaged g{x, xs, c0, (unsigned)S};
     const int lane = threadIdx.x & 31;
     double r0 = 0.0, r1 = 0.0;
-    // claim the next workload (and fetch its descriptor) while this one runs
-    unsigned wn = 0;
-    if (lane == 0) wn = atomicAdd(pv.sched, 1u);
-    wn = __shfl_sync(kFull, wn, 0);
-    Workload dn;
-    if (wn < (unsigned)pv.nwl) dn = pv.wl[wn];
-    while (wn < (unsigned)pv.nwl) {
-        const Workload d = dn;
-        if (lane == 0) wn = atomicAdd(pv.sched, 1u);
-        wn = __shfl_sync(kFull, wn, 0);
-        if (wn < (unsigned)pv.nwl) dn = pv.wl[wn];
-        do_workload<MODE>(d, pv, sv, g, E, x, y, red, lane, r0, r1);
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(pv.sched, 1u);
+        w = __shfl_sync(kFull, w, 0);
+        if (w >= (unsigned)pv.nwl) break;
+        do_workload<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, r0, r1);
     }
     if (lane == 0) {
         const unsigned done = atomicAdd(pv.sched + 1, 1u);
@@ -560,110 +554,75 @@ __device__ __forceinline__ void tma_copy_1d(void *dst, const void *src, uint32_t
 constexpr int kTmaSteps = kTmaChunk / 256;        // 32-slot steps per chunk
 constexpr uint32_t kTmaWaitLimit = 1u << 22;      // try_wait rounds before giving up
 
-// The warp's stream: the slot regions of the workloads it claims, in claim
-// order.  `issued` / `consumed` count chunks over the whole stream; chunk k
-// lives in stage k % kTmaStages and completes phase (k / kTmaStages) & 1.
-struct TmaStream {
+struct TmaRing {
     char *buf;            // kTmaStages x kTmaChunk bytes of this warp
     uint64_t *bar;        // kTmaStages barriers of this warp
-    uint32_t issued, consumed;
+    uint32_t used;        // chunks this warp has consumed so far (all workloads)
     bool fail;
 };
 
-// A claimed workload (w < 0: none).  The next one is claimed while the
-// current one runs, so its first chunks are already in flight when it starts.
-struct WorkSlot {
-    int32_t w;
-    Workload d;
-    const char *src;
-    uint32_t bytes, nch, issued;
-};
-
-__device__ __forceinline__ void claim(WorkSlot &q, const PartView &pv, int lane)
+// Issue chunk c of the region `src` (bytes total) into its stage.
+__device__ __forceinline__ void tma_issue(TmaRing &R, const char *src, uint32_t bytes, uint32_t c)
 {
-    unsigned w = 0;
-    if (lane == 0) w = atomicAdd(pv.sched, 1u);
-    w = __shfl_sync(kFull, w, 0);
-    q.w = w < (unsigned)pv.nwl ? (int)w : -1;
-    q.issued = q.nch = q.bytes = 0;
-    q.src = nullptr;
-    if (q.w >= 0) {
-        q.d = pv.wl[q.w];
-        const int hp = q.d.major == 0 ? q.d.h : (q.d.h + 31) & ~31;
-        q.bytes = (uint32_t)((int64_t)hp * q.d.w * 8);
-        q.nch = (q.bytes + kTmaChunk - 1) / kTmaChunk;
-        q.src = reinterpret_cast<const char *>(pv.slab + q.d.slab);
-    }
+    const uint32_t k = R.used + c, st = k % kTmaStages;
+    const uint32_t n = min((uint32_t)kTmaChunk, bytes - c * kTmaChunk);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(R.bar + st, n);
+    tma_copy_1d(R.buf + st * kTmaChunk, src + (size_t)c * kTmaChunk, n, R.bar + st);
 }
 
-// Keep kTmaStages chunks in flight: the current workload's, then the next's.
-__device__ __forceinline__ void tma_fill(TmaStream &S, WorkSlot &cur, WorkSlot &nxt, int lane)
+__device__ __forceinline__ bool tma_wait(TmaRing &R, uint32_t c)
 {
-    while (S.issued - S.consumed < (uint32_t)kTmaStages) {
-        WorkSlot *q = cur.issued < cur.nch ? &cur : (nxt.w >= 0 && nxt.issued < nxt.nch ? &nxt : nullptr);
-        if (!q) break;
-        if (lane == 0) {
-            const uint32_t st = S.issued % kTmaStages;
-            const uint32_t n = min((uint32_t)kTmaChunk, q->bytes - q->issued * kTmaChunk);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive_expect_tx(S.bar + st, n);
-            tma_copy_1d(S.buf + st * kTmaChunk, q->src + (size_t)q->issued * kTmaChunk, n, S.bar + st);
-        }
-        ++q->issued;
-        ++S.issued;
-    }
-}
-
-__device__ __forceinline__ bool tma_wait(TmaStream &S, uint32_t k)
-{
-    const uint32_t st = k % kTmaStages, parity = (k / kTmaStages) & 1u;
+    const uint32_t k = R.used + c, st = k % kTmaStages, parity = (k / kTmaStages) & 1u;
     for (uint32_t it = 0; it < kTmaWaitLimit; ++it)
-        if (mbar_try_wait(S.bar + st, parity)) return true;
+        if (mbar_try_wait(R.bar + st, parity)) return true;
     return false;
 }
 
 template <int MODE, class G>
-__device__ __forceinline__ void do_workload_tma(WorkSlot &cur, WorkSlot &nxt, const PartView &pv,
+__device__ __forceinline__ void do_workload_tma(const Workload &d, const PartView &pv,
                                                 const SplitView &sv, const G &g, const Epi &E,
                                                 const float *__restrict__ x,
                                                 float *__restrict__ y, double2 *red, int lane,
-                                                TmaStream &S, double &r0, double &r1)
+                                                TmaRing &R, double &r0, double &r1)
 {
-    const Workload &d = cur.d;
     const uint32_t *__restrict__ rows = pv.rows + d.rows;
     const int hp = d.major == 0 ? d.h : (d.h + 31) & ~31;
+    const uint32_t bytes = (uint32_t)((int64_t)hp * d.w * 8);
+    const uint32_t nch = (bytes + kTmaChunk - 1) / kTmaChunk;
+    const char *src = reinterpret_cast<const char *>(pv.slab + d.slab);
+    if (lane == 0)
+        for (uint32_t c = 0; c < nch && c < (uint32_t)kTmaStages; ++c) tma_issue(R, src, bytes, c);
+    // steps per row (row-major) or per 32-row block (column-major)
+    const int per = d.major == 0 ? (d.w >> 5) : d.w;
+    int left = per;                // steps left in the current row / block
+    int unit = 0;                  // current row (row-major) or block (column-major)
     RowPre mine = prefetch_row<MODE>(E, rows, lane, lane < d.h, x, y);
-    if (cur.nch == 0) {            // rows without entries (w = 0)
+    float acc = 0.f;
+    if (nch == 0) {                // rows without entries (w = 0)
         for (int b = 0; b < hp; b += 32) {
             if (b > 0) mine = prefetch_row<MODE>(E, rows, b + lane, b + lane < d.h, x, y);
             if (b + lane < d.h) finish_row_pre<MODE>(E, sv, red, mine, 0.f, x, y, r0, r1);
         }
         return;
     }
-    // steps per row (row-major) or per 32-row block (column-major)
-    const int per = d.major == 0 ? (d.w >> 5) : d.w;
-    int left = per, unit = 0;
-    float acc = 0.f;
-    for (uint32_t c = 0; c < cur.nch; ++c) {
-        tma_fill(S, cur, nxt, lane);
-        if (!tma_wait(S, S.consumed)) {
-            // give up: record it, let the copies still in flight land (each
-            // wait bounded again), then stop this warp
-            S.fail = true;
-            for (uint32_t k = S.consumed + 1; k < S.issued; ++k) tma_wait(S, k);
-            S.consumed = S.issued;
-            return;
+    for (uint32_t c = 0; c < nch; ++c) {
+        if (!tma_wait(R, c)) {
+            // give up: record it, then let the copies still in flight land
+            // (each wait bounded again) before the warp leaves its ring
+            R.fail = true;
+            for (uint32_t q = c + 1; q < nch && q < c + kTmaStages; ++q) tma_wait(R, q);
+            break;
         }
-        const uint32_t st = S.consumed % kTmaStages;
-        const uint2 *ch = reinterpret_cast<const uint2 *>(S.buf + st * kTmaChunk);
-        const int steps = (int)min((uint32_t)kTmaSteps, (cur.bytes - c * kTmaChunk) / 256u);
+        const uint32_t st = (R.used + c) % kTmaStages;
+        const uint2 *ch = reinterpret_cast<const uint2 *>(R.buf + st * kTmaChunk);
+        const int steps = (int)min((uint32_t)kTmaSteps, (bytes - c * kTmaChunk) / 256u);
         uint2 sl[kTmaSteps];
         float xv[kTmaSteps];
 #pragma unroll
         for (int j = 0; j < kTmaSteps; ++j) sl[j] = j < steps ? ch[j * 32 + lane] : make_uint2(0xffffffffu, 0u);
         __syncwarp();
-        ++S.consumed;
-        tma_fill(S, cur, nxt, lane);
+        if (lane == 0 && c + kTmaStages < nch) tma_issue(R, src, bytes, c + kTmaStages);
 #pragma unroll
         for (int j = 0; j < kTmaSteps; ++j) xv[j] = (int)sl[j].x >= 0 ? g((int)sl[j].x) : 0.f;
 #pragma unroll
@@ -687,6 +646,7 @@ __device__ __forceinline__ void do_workload_tma(WorkSlot &cur, WorkSlot &nxt, co
             acc = 0.f;
         }
     }
+    R.used += nch;
 }
 
 // One persistent 32-warp block per SM: x[c0, c0 + xs_cols) in shared memory
@@ -707,37 +667,32 @@ k_part_tma(PartView pv, SplitView sv, const float *__restrict__ xin, float *__re
     Epi E = load_epi<MODE>(st);
     resolve_xy<MODE>(st, x, y);
     if (MODE == EPI_ADJ) E.xs = x[E.seed];
-    const int S0 = pv.xs_cols, c0 = pv.c0;
-    if (((c0 | S0) & 3) == 0) {
+    const int S = pv.xs_cols, c0 = pv.c0;
+    if (((c0 | S) & 3) == 0) {
         const float4 *src4 = reinterpret_cast<const float4 *>(x + c0);
         float4 *dst4 = reinterpret_cast<float4 *>(xs);
-        for (int i = threadIdx.x; i < (S0 >> 2); i += blockDim.x) dst4[i] = __ldg(src4 + i);
+        for (int i = threadIdx.x; i < (S >> 2); i += blockDim.x) dst4[i] = __ldg(src4 + i);
     } else {
-        for (int i = threadIdx.x; i < S0; i += blockDim.x) xs[i] = __ldg(x + c0 + i);
+        for (int i = threadIdx.x; i < S; i += blockDim.x) xs[i] = __ldg(x + c0 + i);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    TmaStream S{ring + warp * kTmaStages * kTmaChunk, bars + warp * kTmaStages, 0u, 0u, false};
+    TmaRing R{ring + warp * kTmaStages * kTmaChunk, bars + warp * kTmaStages, 0u, false};
     if (lane == 0) {
-        for (int q = 0; q < kTmaStages; ++q) mbar_init(S.bar + q, 1);
+        for (int s2 = 0; s2 < kTmaStages; ++s2) mbar_init(R.bar + s2, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const GatherStaged g{x, xs, c0, (unsigned)S0};
+    const GatherStaged g{x, xs, c0, (unsigned)S};
     double r0 = 0.0, r1 = 0.0;
-    WorkSlot cur, nxt;
-    claim(cur, pv, lane);
-    nxt.w = -1;
-    nxt.issued = nxt.nch = nxt.bytes = 0;
-    if (cur.w >= 0) claim(nxt, pv, lane);
-    while (cur.w >= 0 && !S.fail) {
-        do_workload_tma<MODE>(cur, nxt, pv, sv, g, E, x, y, red, lane, S, r0, r1);
-        if (S.fail) break;
-        cur = nxt;
-        if (cur.w >= 0) claim(nxt, pv, lane);
-        else nxt.w = -1;
+    for (;;) {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(pv.sched, 1u);
+        w = __shfl_sync(kFull, w, 0);
+        if (w >= (unsigned)pv.nwl || R.fail) break;
+        do_workload_tma<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, R, r0, r1);
     }
     if (lane == 0) {
-        if (S.fail) atomicOr(pv.status, 1u);
+        if (R.fail) atomicOr(pv.status, 1u);
         const unsigned done = atomicAdd(pv.sched + 1, 1u);
         if (done == gridDim.x * (blockDim.x >> 5) - 1) {   // every warp has left the loop
             pv.sched[0] = 0u;
