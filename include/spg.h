@@ -146,6 +146,11 @@ typedef struct {
      * slots into a shared-memory ring with TMA bulk copies (24K x columns
      * staged; measured slower at R-MAT scale 22: 0.33 ms vs 0.23 ms). */
     int kernel;
+    /* PAGERANK handles only: store column indices alone (4 bytes per slot
+     * instead of 8).  M = A^T diag(1/outdeg), so the iteration gathers
+     * z = p * (1/outdeg) and the epilogue writes both p and z; spmv scales x
+     * first.  rwr and spmm need stored values and refuse such handles. */
+    int pattern_only;
 } spg_build_opts;
 
 /* Per-call results of the power iterations. */

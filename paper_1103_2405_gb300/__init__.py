@@ -44,7 +44,7 @@ class _Opts(ctypes.Structure):
                 ("keep_csr", ctypes.c_int), ("device", ctypes.c_int), ("split_cost", ctypes.c_double),
                 ("tune_table_path", ctypes.c_char_p), ("x_stage_cols", ctypes.c_int64),
                 ("slab_prefetch", ctypes.c_int64), ("loop_mode", ctypes.c_int),
-                ("max_rows", ctypes.c_int64), ("kernel", ctypes.c_int)]
+                ("max_rows", ctypes.c_int64), ("kernel", ctypes.c_int), ("pattern_only", ctypes.c_int)]
 
 
 class IterInfo(ctypes.Structure):
@@ -197,7 +197,8 @@ class Format:
     def __init__(self, rowptr, col, val=None, kind="pagerank", tile_width=0, wl=0, heavy_row=-1,
                  layout_rule=1, max_warps=0, vec_width=1, build_transpose=False, keep_plan=False,
                  keep_csr=False, host_only=False, split_cost=0.0, table=None, x_stage_cols=0,
-                 slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, stream=None):
+                 slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, pattern_only=False,
+                 stream=None):
         L = lib()
         self._h = ctypes.c_void_p(None)
         on_dev = _is_torch(rowptr) and rowptr.is_cuda
@@ -217,7 +218,8 @@ class Format:
                      int(vec_width), int(bool(build_transpose)), int(bool(keep_plan)),
                      int(bool(keep_csr)), -1 if host_only else 0, float(split_cost),
                      None if tpath is None else str(tpath).encode(), int(x_stage_cols),
-                     int(slab_prefetch), int(loop_mode), int(max_rows), int(kernel))
+                     int(slab_prefetch), int(loop_mode), int(max_rows), int(kernel),
+                     int(bool(pattern_only)))
         _check(L.spg_build_format(ctypes.byref(csr), KIND[kind], ctypes.byref(opts),
                                   _stream(stream), ctypes.byref(self._h)))
         self.kind = kind
@@ -433,7 +435,7 @@ class BatchFormat:
         opts = _Opts(0, 0, int(heavy_row), int(layout_rule), int(max_warps), 1, 0, 0, 0,
                      -1 if host_only else 0, 0.0, None if tpath is None else str(tpath).encode(),
                      int(x_stage_cols), int(slab_prefetch), int(loop_mode), int(max_rows),
-                     int(kernel))
+                     int(kernel), 0)
         self._h = ctypes.c_void_p(None)
         _check(L.spg_build_batch(ctypes.cast(arr, ctypes.c_void_p), len(graphs), ctypes.byref(opts),
                                  _stream(stream), ctypes.byref(self._h)))

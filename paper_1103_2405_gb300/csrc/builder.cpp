@@ -504,7 +504,15 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
     L.padded_slots = nslab;
     L.wl.resize((size_t)nwl_all);
     L.rows.resize((size_t)nrows_all);
-    L.slab.resize((size_t)nslab);
+    L.pattern = prm.pattern_only;
+    if (L.pattern) {
+        L.slab4.resize((size_t)nslab);
+        L.inv_deg.assign((size_t)N, 0.f);
+        for (int64_t j = 0; j < N; ++j)
+            if (src.colptr[j + 1] > src.colptr[j]) L.inv_deg[(size_t)L.perm[(size_t)j]] = src.val[src.colptr[j]];
+    } else {
+        L.slab.resize((size_t)nslab);
+    }
     if (prm.track_edges) L.edge_slot.assign((size_t)nnz, -1);
 
     // split rows (ascending row id per part) and their chunk slots
@@ -603,7 +611,8 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
                             v.x = 0xffffffffu;
                             v.y = 0u;
                         }
-                        L.slab[(size_t)slot] = v;
+                        if (L.pattern) L.slab4[(size_t)slot] = v.x;
+                        else L.slab[(size_t)slot] = v;
                     }
                 }
             }
@@ -665,7 +674,8 @@ cudaError_t upload_layout(Layout &L, bool keep_host, cudaStream_t s)
     SPG_UP(d_inv, inv);
     SPG_UP(d_wl, wl);
     SPG_UP(d_rows, rows);
-    SPG_UP(d_slab, slab);
+    if (L.pattern) { SPG_UP(d_slab4, slab4); SPG_UP(d_inv_deg, inv_deg); }
+    else SPG_UP(d_slab, slab);
     SPG_UP(d_split, split);
     SPG_UP(d_slot_owner, slot_owner);
     if (!L.edge_slot.empty()) SPG_UP(d_edge_slot, edge_slot);
@@ -682,6 +692,7 @@ cudaError_t upload_layout(Layout &L, bool keep_host, cudaStream_t s)
         std::vector<Workload>().swap(L.wl);
         std::vector<uint32_t>().swap(L.rows);
         std::vector<uint2>().swap(L.slab);
+        std::vector<uint32_t>().swap(L.slab4);
     }
     return cudaSuccess;
 }
@@ -690,7 +701,8 @@ void Layout::free_device()
 {
     cudaFree(d_perm); cudaFree(d_inv); cudaFree(d_wl); cudaFree(d_rows); cudaFree(d_slab);
     cudaFree(d_split); cudaFree(d_slot_owner); cudaFree(d_partial); cudaFree(d_counter);
-    cudaFree(d_edge_slot);
+    cudaFree(d_edge_slot); cudaFree(d_slab4); cudaFree(d_inv_deg);
+    d_slab4 = nullptr; d_inv_deg = nullptr;
     d_perm = d_inv = nullptr; d_wl = nullptr; d_rows = nullptr; d_slab = nullptr;
     d_split = nullptr; d_slot_owner = nullptr; d_partial = nullptr; d_counter = nullptr;
     d_edge_slot = nullptr;
@@ -705,6 +717,7 @@ std::vector<PartView> Layout::part_views() const
         pv.wl = d_wl + ph.wl_off;
         pv.rows = d_rows;
         pv.slab = d_slab;
+        pv.slab4 = d_slab4;
         pv.nwl = (int32_t)ph.nwl_total;
         pv.nblocks = ph.nblocks;
         pv.red_base = ph.red_base;

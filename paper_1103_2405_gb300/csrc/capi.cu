@@ -113,6 +113,7 @@ struct spg_format_t {
     DevBuf<int32_t> seeds;
     DevBuf<float> X, Y;
     DevBuf<float> aux, stage_r;
+    DevBuf<float> z0, z1;        // pattern-only PageRank: gathered iterates
     DevBuf<double> init_part;    // block partials of the start vector's dangling mass
     IterState *d_state = nullptr;
     // launch views of the parts: plain (8-warp blocks) and staged (x slice in smem)
@@ -139,7 +140,7 @@ struct spg_format_t {
 
     spg_format_t()
     {
-        for (DevBuf<float> *b : {&x, &y, &partial_k, &X, &Y}) b->epoch = &epoch;
+        for (DevBuf<float> *b : {&x, &y, &partial_k, &X, &Y, &z0, &z1}) b->epoch = &epoch;
         red.epoch = &epoch;
         redk.epoch = &epoch;
         delta_k.epoch = &epoch;
@@ -171,6 +172,7 @@ struct spg_format_t {
         rt_bwd.sched.release();
         redk.release(); delta_k.release(); l1_k.release(); partial_k.release(); seeds.release();
         X.release(); Y.release(); aux.release(); stage_r.release(); init_part.release();
+        z0.release(); z1.release();
         cudaFree(d_state);
         for (auto &kv : graphs) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -365,6 +367,9 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
         if (o.split_cost > 0) prm.split_cost = o.split_cost;
         prm.keep_plan = o.keep_plan != 0;
         prm.track_edges = kind == SPG_KIND_WEIGHTED;
+        if (o.pattern_only && kind != SPG_KIND_PAGERANK)
+            return fail(SPG_ERR_INVALID, "pattern_only needs a PAGERANK handle");
+        prm.pattern_only = o.pattern_only != 0;
         if (o.tune_table_path) {
             std::string err;
             if (!perf_table_load(o.tune_table_path, perf_table(), err)) return fail(SPG_ERR_INVALID, err);
@@ -577,6 +582,14 @@ extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, in
     std::vector<Workload> wl = L.wl;
     std::vector<uint32_t> rows = L.rows;
     std::vector<uint2> slab = L.slab;
+    if (L.pattern && !L.slab4.empty()) {
+        slab.resize(L.slab4.size());
+        for (size_t i = 0; i < slab.size(); ++i) {
+            slab[i].x = L.slab4[i];
+            float v = (int32_t)L.slab4[i] >= 0 ? L.inv_deg[L.slab4[i]] : 0.f;
+            std::memcpy(&slab[i].y, &v, 4);
+        }
+    }
     if (wl.empty() && L.on_device) {
         int64_t nwl = 0;
         for (const PartHost &p : L.parts) nwl += p.nwl_total;
@@ -588,8 +601,17 @@ extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, in
         slab.resize((size_t)L.padded_slots);
         CK(cudaMemcpy(wl.data(), L.d_wl, nwl * sizeof(Workload), cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(rows.data(), L.d_rows, nrows * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-        if (L.padded_slots)
+        if (L.padded_slots && !L.pattern)
             CK(cudaMemcpy(slab.data(), L.d_slab, L.padded_slots * sizeof(uint2), cudaMemcpyDeviceToHost));
+        if (L.padded_slots && L.pattern) {
+            std::vector<uint32_t> s4((size_t)L.padded_slots);
+            CK(cudaMemcpy(s4.data(), L.d_slab4, L.padded_slots * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < s4.size(); ++i) {
+                slab[i].x = s4[i];
+                float v = (int32_t)s4[i] >= 0 ? L.inv_deg[s4[i]] : 0.f;
+                std::memcpy(&slab[i].y, &v, 4);
+            }
+        }
     }
     int64_t k = 0;
     for (const Workload &d : wl) {
@@ -644,7 +666,7 @@ static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
         pv.pf_ahead = h->pf_ahead;
         pv.status = h->d_status;
         const int64_t width = ph.c1 - ph.c0;
-        if (staged && h->kernel == 3 && ph.nwl_total > 0) {
+        if (staged && h->kernel == 3 && !L.pattern && ph.nwl_total > 0) {
             // TMA-pipelined persistent kernel (x slice when the part is wide enough)
             pv.tma = 1;
             pv.xs_cols = width >= 1024 ? (int32_t)std::min<int64_t>(kTmaMaxCols, width) : 0;
@@ -712,6 +734,7 @@ static void launch_parts_L(spg_handle h, const Layout &L, spg_format_t::LayoutRT
 static void launch_parts(spg_handle h, int mode, const float *x, float *y, const IterState *st,
                          double2 *red, cudaStream_t s)
 {
+    if (h->fwd.pattern) mode = mode == EPI_RAW ? EPI_RAW_PAT : (mode == EPI_PAGERANK ? EPI_PR_PAT : mode);
     const spg_format_t::Views &V = get_views(h, true);
     const SplitView sv = split_of(h, V);
     for (const PartView &pv : V.v) launch_part(mode, pv, sv, x, y, st, red, s);
@@ -722,6 +745,11 @@ extern "C" spg_status spg_spmv_permuted(spg_handle h, const float *xp, float *yp
     if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
     if (!xp || !yp || xp == yp) return fail(SPG_ERR_INVALID, "x and y must be distinct device vectors");
     cudaStream_t s = (cudaStream_t)stream;
+    if (h->fwd.pattern) {           // slots hold no values: fold them into x first
+        CK(h->x.ensure((size_t)h->fwd.n));
+        launch_scale(h->fwd.n, xp, h->fwd.d_inv_deg, h->x.p, s);
+        xp = h->x.p;
+    }
     launch_parts(h, EPI_RAW, xp, yp, nullptr, nullptr, s);
     CK(cudaGetLastError());
     return SPG_OK;
@@ -745,7 +773,8 @@ extern "C" spg_status spg_spmv(spg_handle h, const float *x, float *y, float alp
         yd = h->stage_out.p;
         if (beta != 0.f) CK(cudaMemcpyAsync(yd, y, N * sizeof(float), cudaMemcpyHostToDevice, s));
     }
-    launch_gather(N, h->fwd.d_inv, xd, h->x.p, s);
+    if (h->fwd.pattern) launch_gather_scaled(N, h->fwd.d_inv, xd, h->fwd.d_inv_deg, h->x.p, s);
+    else launch_gather(N, h->fwd.d_inv, xd, h->x.p, s);
     launch_parts(h, EPI_RAW, h->x.p, h->y.p, nullptr, nullptr, s);
     launch_scatter_axpby(N, h->fwd.d_inv, h->y.p, yd, alpha, beta, s);
     CK(cudaGetLastError());
@@ -762,6 +791,7 @@ extern "C" spg_status spg_spmm(spg_handle h, const float *X, int64_t ldx, float 
     if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
     if (!X || !Y || k < 1 || k > 1024 || ldx < k || ldy < k) return fail(SPG_ERR_INVALID, "bad SpMM arguments");
     if (!is_device_ptr(X) || !is_device_ptr(Y)) return fail(SPG_ERR_INVALID, "spmm takes device pointers");
+    if (h->fwd.pattern) return fail(SPG_ERR_UNSUPPORTED, "spmm needs stored values (build without pattern_only)");
     cudaStream_t s = (cudaStream_t)stream;
     const Layout &L = h->fwd;
     const int64_t N = L.n;
@@ -913,7 +943,14 @@ extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int 
     const int64_t N = h->fwd.n;
     spg_status st = ensure_vectors(h, N);
     if (st != SPG_OK) return st;
+    const bool pat = h->fwd.pattern;
+    if (pat) { CK(h->z0.ensure((size_t)N)); CK(h->z1.ensure((size_t)N)); }
     IterState hs = make_state(h, damping, tol, max_iter, N, h->x.p, h->y.p);
+    if (pat) {
+        hs.zbuf[0] = h->z0.p;
+        hs.zbuf[1] = h->z1.p;
+        hs.inv_deg = h->fwd.d_inv_deg;
+    }
     CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
     if (p0) {
         const float *pd;
@@ -922,11 +959,12 @@ extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int 
     } else {
         launch_fill(N, (float)(1.0 / (double)N), h->x.p, s);
     }
+    if (pat) launch_scale(N, h->x.p, h->fwd.d_inv_deg, h->z0.p, s);
     CK(h->init_part.ensure((size_t)init_delta_scratch()));
-        launch_init_delta(h->d_state, h->init_part.p, s);
+    launch_init_delta(h->d_state, h->init_part.p, s);
     LoopGraph *g;
     const int nred = nred_of(h, get_views(h, true));
-    st = get_loop_graph(h, "pagerank", [&](cudaStream_t cs, unsigned long long cond, int uc) {
+    st = get_loop_graph(h, pat ? "pagerank_pattern" : "pagerank", [&](cudaStream_t cs, unsigned long long cond, int uc) {
         launch_parts(h, EPI_PAGERANK, nullptr, nullptr, h->d_state, h->red.p, cs);
         launch_check(EPI_PAGERANK, h->d_state, h->red.p, nred, cond, uc, cs);
     }, &g);
@@ -984,6 +1022,7 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
     if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
     if (h->kind != SPG_KIND_PAGERANK && !(h->kind == SPG_KIND_WEIGHTED && k == 1))
         return fail(SPG_ERR_UNSUPPORTED, "rwr needs a PAGERANK handle (or WEIGHTED with k = 1)");
+    if (h->fwd.pattern) return fail(SPG_ERR_UNSUPPORTED, "rwr needs stored values (build without pattern_only)");
     if (!seeds || !R || k < 1 || k > 64 || !(restart > 0.f && restart <= 1.f) || max_iter < 0)
         return fail(SPG_ERR_INVALID, "bad rwr arguments (1 <= k <= 64)");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1136,8 +1175,9 @@ extern "C" spg_status spg_time_parts(spg_handle h, int mode, int reps, float *ms
     for (size_t p = 0; p < pvs.size(); ++p) {
         CK(cudaEventRecord(h->ev0, s));
         for (int r = 0; r < reps; ++r) {
-            if (mode == 0) launch_part(EPI_RAW, pvs[p], sv, h->x.p, h->y.p, nullptr, nullptr, s);
-            else launch_part(EPI_PAGERANK, pvs[p], sv, nullptr, nullptr, h->d_state, h->red.p, s);
+            const bool pat = h->fwd.pattern;
+            if (mode == 0) launch_part(pat ? EPI_RAW_PAT : EPI_RAW, pvs[p], sv, h->x.p, h->y.p, nullptr, nullptr, s);
+            else launch_part(pat ? EPI_PR_PAT : EPI_PAGERANK, pvs[p], sv, nullptr, nullptr, h->d_state, h->red.p, s);
         }
         CK(cudaEventRecord(h->ev1, s));
         CK(cudaEventSynchronize(h->ev1));
@@ -1194,6 +1234,7 @@ extern "C" spg_status spg_spmv_permuted_noalloc(spg_handle h, const float *x_per
     if (!x_perm || !y_perm || x_perm == y_perm)
         return fail(SPG_ERR_INVALID, "x and y must be distinct device vectors");
     const Layout &L = h->fwd;
+    if (L.pattern) return fail(SPG_ERR_UNSUPPORTED, "pattern_only handles: use spg_spmv_permuted");
     if ((int64_t)L.parts.size() > kNoAllocMaxParts || L.nsplit > kNoAllocMaxSplitRows ||
         L.nchunk_slots > kNoAllocMaxChunks)
         return fail(SPG_ERR_INVALID,

@@ -35,6 +35,9 @@ struct BuildParams {
     double split_cost = 2e-7;
     bool keep_plan = false;
     bool track_edges = false;
+    // store column indices only (every column's entries share one value,
+    // kept per column in inv_deg): 4 bytes per slot instead of 8
+    bool pattern_only = false;
     // block-diagonal union of independent graphs: node segments
     // [seg_off[g], seg_off[g+1]); the degree order is taken within each segment
     const int64_t *seg_off = nullptr;
@@ -70,6 +73,9 @@ struct Layout {
     std::vector<Workload> wl;
     std::vector<uint32_t> rows;
     std::vector<uint2> slab;
+    std::vector<uint32_t> slab4;        // pattern-only slots
+    std::vector<float> inv_deg;         // pattern-only: column value, permuted order
+    bool pattern = false;
     std::vector<SplitRow> split;
     std::vector<int32_t> slot_owner;
     std::vector<int64_t> edge_slot;     // edge id -> slab slot (track_edges)
@@ -78,6 +84,8 @@ struct Layout {
     Workload *d_wl = nullptr;
     uint32_t *d_rows = nullptr;
     uint2 *d_slab = nullptr;
+    uint32_t *d_slab4 = nullptr;
+    float *d_inv_deg = nullptr;
     SplitRow *d_split = nullptr;
     int32_t *d_slot_owner = nullptr;
     float *d_partial = nullptr;

@@ -69,6 +69,8 @@ struct Epi {
     const int32_t *gid;
     const float *gbase;
     float xs;            // adjoint: x[seed] of the current launch
+    float *znew;         // pattern-only PageRank: z of the new iterate
+    const float *invdeg;
 };
 
 template <int MODE>
@@ -77,7 +79,7 @@ __device__ __forceinline__ Epi load_epi(const IterState *st)
     Epi E;
     E.c = 1.f; E.base = 0.f; E.tele = 0.f; E.seed = -1; E.dstart = 0;
     E.sc[0] = E.sc[1] = 1.f; E.hnorm = 2; E.aux = nullptr; E.gid = nullptr; E.gbase = nullptr;
-    E.xs = 0.f;
+    E.xs = 0.f; E.znew = nullptr; E.invdeg = nullptr;
     if (MODE == EPI_BATCH) {
         E.c = (float)st->c;
         E.gid = st->gid;
@@ -86,11 +88,15 @@ __device__ __forceinline__ Epi load_epi(const IterState *st)
         E.c = (float)st->c;
         E.seed = st->seed;
         E.aux = st->aux;
-    } else if (MODE == EPI_PAGERANK || MODE == EPI_RWR) {
+    } else if (MODE == EPI_PAGERANK || MODE == EPI_RWR || MODE == EPI_PR_PAT) {
         const double c = st->c, d = st->delta;
         E.c = (float)c;
         E.dstart = st->dangling_start;
-        if (MODE == EPI_PAGERANK) E.base = (float)((c * d + (1.0 - c)) * st->inv_n);
+        if (MODE == EPI_PR_PAT) {
+            E.znew = st->zbuf[st->parity ^ 1];
+            E.invdeg = st->inv_deg;
+        }
+        if (MODE != EPI_RWR) E.base = (float)((c * d + (1.0 - c)) * st->inv_n);
         else { E.tele = (float)(c * d + (1.0 - c)); E.seed = st->seed; }
     } else if (MODE == EPI_HITS) {
         E.sc[0] = (float)st->scale[0];
@@ -109,12 +115,13 @@ __device__ __forceinline__ void epilogue(const Epi &E, uint32_t rid, float tot,
     const uint32_t v = rid & kRowIdMask;
     if (rid & kRowNotFirst) tot += y[v];
     if (rid & kRowNotLast) { y[v] = tot; return; }
-    if (MODE == EPI_RAW) {
+    if (MODE == EPI_RAW || MODE == EPI_RAW_PAT) {
         y[v] = tot;
-    } else if (MODE == EPI_PAGERANK || MODE == EPI_RWR) {
-        float add = MODE == EPI_PAGERANK ? E.base : ((int)v == E.seed ? E.tele : 0.f);
+    } else if (MODE == EPI_PAGERANK || MODE == EPI_RWR || MODE == EPI_PR_PAT) {
+        float add = MODE != EPI_RWR ? E.base : ((int)v == E.seed ? E.tele : 0.f);
         float f = fmaf(E.c, tot, add);
         y[v] = f;
+        if (MODE == EPI_PR_PAT) E.znew[v] = f * __ldg(E.invdeg + v);
         r0 += fabs((double)f - (double)x[v]);
         if ((int64_t)v >= E.dstart) r1 += (double)f;
     } else if (MODE == EPI_BATCH) {
@@ -155,7 +162,8 @@ __device__ __noinline__ void finish_split(const Epi &E, const SplitView &sv, dou
     sv.counter[s] = 0u;
     double r0 = 0.0, r1 = 0.0;
     epilogue<MODE>(E, sr.row, tot, x, y, r0, r1);
-    if (MODE != EPI_RAW && MODE != EPI_BATCH) red[sv.red_split_base + sr.red_slot] = make_double2(r0, r1);
+    if (MODE != EPI_RAW && MODE != EPI_RAW_PAT && MODE != EPI_BATCH)
+        red[sv.red_split_base + sr.red_slot] = make_double2(r0, r1);
 }
 
 template <int MODE>
@@ -188,7 +196,8 @@ __device__ __forceinline__ RowPre prefetch_row(const Epi &E, const uint32_t *__r
     const uint32_t v = p.rid & kRowIdMask;
     if (p.rid & kRowNotFirst) p.yv = y[v];
     if (!(p.rid & kRowNotLast)) {
-        if (MODE == EPI_PAGERANK || MODE == EPI_RWR || MODE == EPI_ADJ) p.xv = x[v];
+        if (MODE == EPI_PAGERANK || MODE == EPI_RWR || MODE == EPI_ADJ || MODE == EPI_PR_PAT) p.xv = x[v];
+        if (MODE == EPI_PR_PAT) p.av = __ldg(E.invdeg + v);
         if (MODE == EPI_ADJ) p.av = __ldg(E.aux + v);
         if (MODE == EPI_BATCH) p.av = __ldg(E.gbase + __ldg(E.gid + v));
     }
@@ -214,12 +223,13 @@ __device__ __forceinline__ void epilogue_pre(const Epi &E, const RowPre &p, floa
     const uint32_t rid = p.rid, v = rid & kRowIdMask;
     if (rid & kRowNotFirst) tot += p.yv;
     if (rid & kRowNotLast) { y[v] = tot; return; }
-    if (MODE == EPI_RAW) {
+    if (MODE == EPI_RAW || MODE == EPI_RAW_PAT) {
         y[v] = tot;
-    } else if (MODE == EPI_PAGERANK || MODE == EPI_RWR) {
-        float add = MODE == EPI_PAGERANK ? E.base : ((int)v == E.seed ? E.tele : 0.f);
+    } else if (MODE == EPI_PAGERANK || MODE == EPI_RWR || MODE == EPI_PR_PAT) {
+        float add = MODE != EPI_RWR ? E.base : ((int)v == E.seed ? E.tele : 0.f);
         float f = fmaf(E.c, tot, add);
         y[v] = f;
+        if (MODE == EPI_PR_PAT) E.znew[v] = f * p.av;
         r0 += fabs((double)f - (double)p.xv);
         if ((int64_t)v >= E.dstart) r1 += (double)f;
     } else if (MODE == EPI_BATCH) {
@@ -314,6 +324,29 @@ struct SlabPrefetch {
     }
 };
 
+// Slot loaders of a workload's region: the full layout stores {column,
+// value} pairs (8 bytes); the pattern-only layout stores the column alone (4
+// bytes) and every slot's value is 1 -- the column's value is folded into
+// the gathered vector (z = p * inv_deg for PageRank).  Both hand back a
+// {column, float bits} pair, padding as column -1.
+constexpr bool is_pattern(int mode) { return mode == EPI_PR_PAT || mode == EPI_RAW_PAT; }
+
+template <bool PAT> struct Slots;
+template <> struct Slots<false> {
+    static constexpr int kBytes = 8;
+    const uint2 *__restrict__ p;
+    __device__ __forceinline__ Slots(const PartView &pv, int64_t off) : p(pv.slab + off) {}
+    __device__ __forceinline__ uint2 ld(int64_t i) const { return __ldcs(p + i); }
+    __device__ __forceinline__ const char *bytes_at(int64_t i) const { return reinterpret_cast<const char *>(p + i); }
+};
+template <> struct Slots<true> {
+    static constexpr int kBytes = 4;
+    const uint32_t *__restrict__ p;
+    __device__ __forceinline__ Slots(const PartView &pv, int64_t off) : p(pv.slab4 + off) {}
+    __device__ __forceinline__ uint2 ld(int64_t i) const { return make_uint2(__ldcs(p + i), 0x3f800000u); }
+    __device__ __forceinline__ const char *bytes_at(int64_t i) const { return reinterpret_cast<const char *>(p + i); }
+};
+
 // One workload (Solution 3) computed by the calling warp.
 template <int MODE, class G>
 __device__ __forceinline__ void do_workload(const Workload &d, const PartView &pv,
@@ -322,10 +355,10 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
                                             double2 *red, int lane, double &r0, double &r1)
 {
     const uint32_t *__restrict__ rows = pv.rows + d.rows;
-    const uint2 *__restrict__ slab = pv.slab + d.slab;
+    const Slots<is_pattern(MODE)> slab{pv, d.slab};
     const int hp = d.major == 0 ? d.h : (d.h + 31) & ~31;
-    SlabPrefetch pf{reinterpret_cast<const char *>(slab), (unsigned)((int64_t)hp * d.w * 8), 0u,
-                    (unsigned)pv.pf_ahead};
+    SlabPrefetch pf{slab.bytes_at(0), (unsigned)((int64_t)hp * d.w * Slots<is_pattern(MODE)>::kBytes),
+                    0u, (unsigned)pv.pf_ahead};
     if (pf.ahead) pf.advance(0u, lane);
     if (d.major == 0) {
         // row-major (CSR-vector): the warp strides across one row at a time;
@@ -335,15 +368,15 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
             const RowPre mine = prefetch_row<MODE>(E, rows, g0 + lane, g0 + lane < d.h, x, y);
             const int gend = min(d.h, g0 + 32);
             for (int i = g0; i < gend; ++i) {
-                const uint2 *s = slab + (int64_t)i * d.w + lane;
+                const int64_t s = (int64_t)i * d.w + lane;
                 float acc = 0.f;
                 int st = 0;
                 if (nst >= 4) {
-                    uint2 a0 = __ldcs(s), a1 = __ldcs(s + 32), a2 = __ldcs(s + 64), a3 = __ldcs(s + 96);
+                    uint2 a0 = slab.ld(s), a1 = slab.ld(s + 32), a2 = slab.ld(s + 64), a3 = slab.ld(s + 96);
                     for (st = 4; st + 4 <= nst; st += 4) {
-                        if (pf.ahead) pf.advance((unsigned)(((int64_t)i * d.w + st * 32) * 8), lane);
-                        const uint2 *q = s + st * 32;
-                        const uint2 b0 = __ldcs(q), b1 = __ldcs(q + 32), b2 = __ldcs(q + 64), b3 = __ldcs(q + 96);
+                        if (pf.ahead) pf.advance((unsigned)(((int64_t)i * d.w + st * 32) * Slots<is_pattern(MODE)>::kBytes), lane);
+                        const int64_t q = s + st * 32;
+                        const uint2 b0 = slab.ld(q), b1 = slab.ld(q + 32), b2 = slab.ld(q + 64), b3 = slab.ld(q + 96);
                         acc = slot_fma_g(a0, g, acc);
                         acc = slot_fma_g(a1, g, acc);
                         acc = slot_fma_g(a2, g, acc);
@@ -359,14 +392,14 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
                     uint2 r[3];
 #pragma unroll
                     for (int u = 0; u < 3; ++u)
-                        r[u] = st + u < nst ? __ldcs(s + (st + u) * 32) : make_uint2(0xffffffffu, 0u);
+                        r[u] = st + u < nst ? slab.ld(s + (st + u) * 32) : make_uint2(0xffffffffu, 0u);
 #pragma unroll
                     for (int u = 0; u < 3; ++u) acc = slot_fma_g(r[u], g, acc);
                 }
                 acc = warp_sum(acc);
                 const RowPre p = shfl_row(mine, i - g0);
                 if (lane == 0) finish_row_pre<MODE>(E, sv, red, p, acc, x, y, r0, r1);
-                if (pf.ahead) pf.advance((unsigned)((int64_t)(i + 1) * d.w * 8), lane);
+                if (pf.ahead) pf.advance((unsigned)((int64_t)(i + 1) * d.w * Slots<is_pattern(MODE)>::kBytes), lane);
             }
         }
     } else {
@@ -376,18 +409,18 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
             const bool two = b + 32 < hp;
             const RowPre pa = prefetch_row<MODE>(E, rows, b + lane, b + lane < d.h, x, y);
             const RowPre pb = prefetch_row<MODE>(E, rows, b + 32 + lane, two && b + 32 + lane < d.h, x, y);
-            const uint2 *sa = slab + (int64_t)b * d.w + lane;
-            const uint2 *sb = sa + (int64_t)32 * d.w;
+            const int64_t sa = (int64_t)b * d.w + lane;
+            const int64_t sb = sa + (int64_t)32 * d.w;
             float acc_a = 0.f, acc_b = 0.f;
             int e = 0;
             if (two) {
                 for (; e + 3 < d.w; e += 4) {
-                    if (pf.ahead) pf.advance((unsigned)(((int64_t)b * d.w + (int64_t)e * 32) * 8), lane);
+                    if (pf.ahead) pf.advance((unsigned)(((int64_t)b * d.w + (int64_t)e * 32) * Slots<is_pattern(MODE)>::kBytes), lane);
                     uint2 a[4], c[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        a[u] = __ldcs(sa + (int64_t)(e + u) * 32);
-                        c[u] = __ldcs(sb + (int64_t)(e + u) * 32);
+                        a[u] = slab.ld(sa + (int64_t)(e + u) * 32);
+                        c[u] = slab.ld(sb + (int64_t)(e + u) * 32);
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -396,16 +429,16 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
                     }
                 }
                 for (; e < d.w; ++e) {
-                    const uint2 a0 = __ldcs(sa + (int64_t)e * 32), c0 = __ldcs(sb + (int64_t)e * 32);
+                    const uint2 a0 = slab.ld(sa + (int64_t)e * 32), c0 = slab.ld(sb + (int64_t)e * 32);
                     acc_a = slot_fma_g(a0, g, acc_a);
                     acc_b = slot_fma_g(c0, g, acc_b);
                 }
             } else {
                 for (; e + 7 < d.w; e += 8) {
-                    if (pf.ahead) pf.advance((unsigned)(((int64_t)b * d.w + (int64_t)e * 32) * 8), lane);
+                    if (pf.ahead) pf.advance((unsigned)(((int64_t)b * d.w + (int64_t)e * 32) * Slots<is_pattern(MODE)>::kBytes), lane);
                     uint2 a[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) a[u] = __ldcs(sa + (int64_t)(e + u) * 32);
+                    for (int u = 0; u < 8; ++u) a[u] = slab.ld(sa + (int64_t)(e + u) * 32);
 #pragma unroll
                     for (int u = 0; u < 8; ++u) acc_a = slot_fma_g(a[u], g, acc_a);
                 }
@@ -413,14 +446,14 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
                     uint2 r[7];
 #pragma unroll
                     for (int u = 0; u < 7; ++u)
-                        r[u] = e + u < d.w ? __ldcs(sa + (int64_t)(e + u) * 32) : make_uint2(0xffffffffu, 0u);
+                        r[u] = e + u < d.w ? slab.ld(sa + (int64_t)(e + u) * 32) : make_uint2(0xffffffffu, 0u);
 #pragma unroll
                     for (int u = 0; u < 7; ++u) acc_a = slot_fma_g(r[u], g, acc_a);
                 }
             }
             if (b + lane < d.h) finish_row_pre<MODE>(E, sv, red, pa, acc_a, x, y, r0, r1);
             if (two && b + 32 + lane < d.h) finish_row_pre<MODE>(E, sv, red, pb, acc_b, x, y, r0, r1);
-            if (pf.ahead) pf.advance((unsigned)((int64_t)(b + 64) * d.w * 8), lane);
+            if (pf.ahead) pf.advance((unsigned)((int64_t)(b + 64) * d.w * Slots<is_pattern(MODE)>::kBytes), lane);
         }
     }
 }
@@ -447,14 +480,16 @@ k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restri
     Epi E = load_epi<MODE>(st);
     resolve_xy<MODE>(st, x, y);
     if (MODE == EPI_ADJ) E.xs = x[E.seed];
+    const float *gsrc = (MODE == EPI_PR_PAT) ? st->zbuf[st->parity] : x;
     const int lane = threadIdx.x & 31;
     const int wid = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     double r0 = 0.0, r1 = 0.0;
     if (wid < pv.nwl) {
-        const GatherGlobal g{x};
+        const GatherGlobal g{gsrc};
         do_workload<MODE>(pv.wl[wid], pv, sv, g, E, x, y, red, lane, r0, r1);
     }
-    if (MODE != EPI_RAW && MODE != EPI_BATCH) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
+    if (MODE != EPI_RAW && MODE != EPI_RAW_PAT && MODE != EPI_BATCH)
+        block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
 }
 
 // Same computation with the part's densest x columns staged in shared
@@ -475,16 +510,17 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
     Epi E = load_epi<MODE>(st);
     resolve_xy<MODE>(st, x, y);
     if (MODE == EPI_ADJ) E.xs = x[E.seed];
+    const float *gsrc = (MODE == EPI_PR_PAT) ? st->zbuf[st->parity] : x;
     const int S = pv.xs_cols, c0 = pv.c0;
     if (((c0 | S) & 3) == 0) {
-        const float4 *src = reinterpret_cast<const float4 *>(x + c0);
+        const float4 *src = reinterpret_cast<const float4 *>(gsrc + c0);
         float4 *dst = reinterpret_cast<float4 *>(xs);
         for (int i = threadIdx.x; i < (S >> 2); i += blockDim.x) dst[i] = __ldg(src + i);
     } else {
-        for (int i = threadIdx.x; i < S; i += blockDim.x) xs[i] = __ldg(x + c0 + i);
+        for (int i = threadIdx.x; i < S; i += blockDim.x) xs[i] = __ldg(gsrc + c0 + i);
     }
     __syncthreads();
-    const GatherStaged g{x, xs, c0, (unsigned)S};
+    const GatherStaged g{gsrc, xs, c0, (unsigned)S};
     const int lane = threadIdx.x & 31;
     double r0 = 0.0, r1 = 0.0;
     for (;;) {
@@ -764,6 +800,8 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
         case EPI_RWR: launch_staged<EPI_RWR>(pv, sv, x, y, st, red, s); break;
         case EPI_ADJ: launch_staged<EPI_ADJ>(pv, sv, x, y, st, red, s); break;
         case EPI_BATCH: launch_staged<EPI_BATCH>(pv, sv, x, y, st, red, s); break;
+        case EPI_PR_PAT: launch_staged<EPI_PR_PAT>(pv, sv, x, y, st, red, s); break;
+        case EPI_RAW_PAT: launch_staged<EPI_RAW_PAT>(pv, sv, x, y, st, red, s); break;
         default: launch_staged<EPI_HITS>(pv, sv, x, y, st, red, s); break;
         }
         count_launches(1);
@@ -776,6 +814,8 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
     case EPI_RWR: k_part<EPI_RWR><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     case EPI_ADJ: k_part<EPI_ADJ><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     case EPI_BATCH: k_part<EPI_BATCH><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
+    case EPI_PR_PAT: k_part<EPI_PR_PAT><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
+    case EPI_RAW_PAT: k_part<EPI_RAW_PAT><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     default: k_part<EPI_HITS><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     }
     count_launches(1);
@@ -1533,6 +1573,35 @@ __global__ void k_fill(int64_t n, float v, float *__restrict__ p)
 void launch_batch_init(int64_t n, const IterState *st, float *x, cudaStream_t s)
 {
     k_batch_init<<<grid_for(n), 256, 0, s>>>(n, st, x);
+    count_launches(1);
+}
+
+__global__ void k_scale(int64_t n, const float *__restrict__ p, const float *__restrict__ d,
+                        float *__restrict__ z)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = p[i] * d[i];
+}
+
+void launch_scale(int64_t n, const float *p, const float *inv_deg, float *z, cudaStream_t s)
+{
+    k_scale<<<grid_for(n), 256, 0, s>>>(n, p, inv_deg, z);
+    count_launches(1);
+}
+
+__global__ void k_gather_scaled(int64_t n, const int32_t *__restrict__ inv, const float *__restrict__ x,
+                                const float *__restrict__ d, float *__restrict__ xp)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        xp[i] = __ldg(x + inv[i]) * d[i];
+}
+
+void launch_gather_scaled(int64_t n, const int32_t *inv, const float *x, const float *inv_deg,
+                          float *xp, cudaStream_t s)
+{
+    k_gather_scaled<<<grid_for(n), 256, 0, s>>>(n, inv, x, inv_deg, xp);
     count_launches(1);
 }
 

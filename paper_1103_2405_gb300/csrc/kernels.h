@@ -13,7 +13,9 @@ enum EpiMode {
     EPI_RWR = 2,       // y' = c (M' x')_v + [v == s](c delta + 1 - c); same sums
     EPI_HITS = 3,      // y' = (M' x')_v * scale[other half];  per-half sum or sum of squares
     EPI_ADJ = 4,       // y' = c (M'^T x')_v + [v dangling] c x'_s + g'_v;  sum |y'-x'|
-    EPI_BATCH = 5      // y' = c (M' x')_v + base[graph of v];  sums in a separate pass
+    EPI_BATCH = 5,     // y' = c (M' x')_v + base[graph of v];  sums in a separate pass
+    EPI_PR_PAT = 6,    // pattern-only PageRank: gathers z, writes p and z = p * inv_deg
+    EPI_RAW_PAT = 7    // pattern-only SpMV: y' = A'^T x' (x' already scaled by inv_deg)
 };
 
 // One tiled-composite launch of one part (Solution 3: one warp per
@@ -48,6 +50,12 @@ int init_delta_scratch();
 void launch_set_one(float *p, const int32_t *idx, int count, cudaStream_t s);
 void launch_init_delta_k(const IterState *st, const float *X, int k, double *delta_k,
                          cudaStream_t s);
+
+// z[i] = p[i] * inv_deg[i] (pattern-only start vectors)
+void launch_scale(int64_t n, const float *p, const float *inv_deg, float *z, cudaStream_t s);
+// xp[k] = x[inv[k]] * inv_deg[k]
+void launch_gather_scaled(int64_t n, const int32_t *inv, const float *x, const float *inv_deg,
+                          float *xp, cudaStream_t s);
 
 // Permutation and vector helpers.
 void launch_gather(int64_t n, const int32_t *inv, const float *x, float *xp, cudaStream_t s);

@@ -53,6 +53,7 @@ struct PartView {
     const Workload *wl;
     const uint32_t *rows;
     const uint2 *slab;
+    const uint32_t *slab4;   // pattern-only layout: column index per slot (value implied)
     uint32_t *sched;      // staged kernel: {next workload, warps done}, zero between launches
     uint32_t *status;     // TMA kernel: set non-zero when a bounded wait ran out
     int32_t nwl;          // workloads incl. zero-row ones
@@ -102,6 +103,9 @@ struct IterState {
     int64_t dangling_start;
     float *buf[2];        // ping-pong iterates (permuted order)
     const float *aux;     // adjoint: the loss gradient g in permuted order
+    // pattern-only PageRank: z = p * inv_deg is the gathered vector
+    float *zbuf[2];
+    const float *inv_deg;
     // batch of independent graphs (block-diagonal union)
     const int32_t *gid;   // graph of each permuted position
     float *gbase;         // per graph: (c * dangling mass + 1 - c) / n_g of the current iterate

@@ -101,6 +101,23 @@ def test_host_plan_matches_oracle(spg, scale, ef, tw, heavy, rule, mw, mr):
     assert np.array_equal(v[got].view(np.uint32), mval[want].view(np.uint32))
 
 
+def test_pattern_only_layout_holds_the_same_matrix(spg):
+    # column indices only; each column's value fl32(1/outdeg) comes back from
+    # the per-column table, so the stored matrix is still exactly M
+    rp, col = graphgen.rmat(11, 8, seed=3)
+    f = spg.Format(rp, col, kind="pagerank", pattern_only=True, host_only=True, max_warps=200,
+                   keep_plan=True)
+    r, c, v = f.export_entries()
+    mrp, mcol, mval = oracle.build_M(rp, col)
+    n = rp.shape[0] - 1
+    got = np.lexsort((c, r))
+    want = np.lexsort((mcol, np.repeat(np.arange(n), np.diff(mrp))))
+    assert np.array_equal(c[got], mcol[want])
+    assert np.array_equal(v[got].view(np.uint32), mval[want].view(np.uint32))
+    with pytest.raises(spg.SpgError):
+        spg.Format(rp, col, kind="hits", pattern_only=True, host_only=True)
+
+
 def test_hits_block_matrix_entries(spg):
     rp, col = graphgen.rmat(9, 8, seed=2)
     n = rp.shape[0] - 1
@@ -132,7 +149,7 @@ def test_malformed_csr_rejected(spg, bad):
         col = np.array([1, 2, 0, 0], np.int32)
     csr = spg._Csr(n, nc, nnz, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(col.ctypes.data),
                    None, 0)
-    opts = spg._Opts(0, 0, -1, 1, 64, 1, 0, 0, 0, -1, 0.0, None, 0, 0, 0, 0, 0)
+    opts = spg._Opts(0, 0, -1, 1, 64, 1, 0, 0, 0, -1, 0.0, None, 0, 0, 0, 0, 0, 0)
     h = ctypes.c_void_p()
     st = L.spg_build_format(ctypes.byref(csr), 1, ctypes.byref(opts), None, ctypes.byref(h))
     assert st == -1 and not h.value

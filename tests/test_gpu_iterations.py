@@ -25,7 +25,9 @@ def g14():
     return rp, col, M, p_star
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(tile_width=2048), dict(tile_width=512, heavy_row=0)])
+@pytest.mark.parametrize("opts", [dict(), dict(tile_width=2048), dict(tile_width=512, heavy_row=0),
+                                  dict(pattern_only=True), dict(pattern_only=True, tile_width=1024),
+                                  dict(kernel=2), dict(kernel=3)])
 def test_pagerank_matches_oracle(g14, opts):
     rp, col, M, p_star = g14
     f = spg.Format(rp, col, kind="pagerank", **opts)

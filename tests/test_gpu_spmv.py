@@ -51,6 +51,10 @@ def _check(y, yref, M, x, tol=1e-5):
 
 CONFIGS = [
     ("rmat14", dict()),                                        # auto: one composite part
+    ("rmat14", dict(pattern_only=True, tile_width=2048)),      # 4-byte slots, values folded into x
+    ("hub", dict(pattern_only=True)),
+    ("rmat14", dict(kernel=2)),                                # plain 8-warp kernel
+    ("rmat14", dict(kernel=3, tile_width=2048)),               # TMA ring kernel
     ("rmat14", dict(tile_width=2048)),                         # dense tiles + sparse tail
     ("rmat14", dict(tile_width=256, heavy_row=0)),             # no split rows
     ("rmat14", dict(tile_width=4096, heavy_row=32, layout_rule=0)),
