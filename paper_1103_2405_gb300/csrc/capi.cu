@@ -660,6 +660,7 @@ static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
         pv.wl = L.d_wl + ph.wl_off;
         pv.rows = L.d_rows;
         pv.slab = L.d_slab;
+        pv.slab4 = L.d_slab4;
         pv.sched = rt.sched.p ? rt.sched.p + 2 * p : nullptr;
         pv.nwl = (int32_t)ph.nwl_total;
         pv.c0 = (int32_t)ph.c0;
@@ -1267,6 +1268,7 @@ extern "C" spg_status spg_spmv_permuted_noalloc(spg_handle h, const float *x_per
         pv.wl = L.d_wl + ph.wl_off;
         pv.rows = L.d_rows;
         pv.slab = L.d_slab;
+        pv.slab4 = L.d_slab4;
         pv.sched = sched + 2 * p;
         pv.nwl = (int32_t)ph.nwl_total;
         pv.c0 = (int32_t)ph.c0;

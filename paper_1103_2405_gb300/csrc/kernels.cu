@@ -537,7 +537,7 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
             pv.sched[1] = 0u;
         }
     }
-    if (MODE != EPI_RAW && MODE != EPI_BATCH) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
+    if (MODE != EPI_RAW && MODE != EPI_RAW_PAT && MODE != EPI_BATCH) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
 }
 
 // ------------------------------------------------ TMA-pipelined kernel --
@@ -735,7 +735,7 @@ k_part_tma(PartView pv, SplitView sv, const float *__restrict__ xin, float *__re
             pv.sched[1] = 0u;
         }
     }
-    if (MODE != EPI_RAW && MODE != EPI_BATCH)
+    if (MODE != EPI_RAW && MODE != EPI_RAW_PAT && MODE != EPI_BATCH)
         block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
 }
 
