@@ -727,7 +727,7 @@ std::vector<PartView> Layout::part_views() const
         pv.pf_ahead = 0;
         pv.status = nullptr;
         pv.tma = 0;
-        pv.pad_ = 0;
+        pv.flat = 0;
         v.push_back(pv);
     }
     return v;

@@ -128,7 +128,7 @@ struct spg_format_t {
     } rt_fwd, rt_bwd;
     int64_t stage_cols = kStagedMaxCols;
     int32_t pf_ahead = 0;        // L2 bulk-prefetch distance of the slot stream (bytes, 0 = off)
-    int kernel = 0;              // 0/1: register stream + staged x slice, 2: plain, 3: TMA ring
+    int kernel = 0;              // 0/1: register stream + staged x slice, 2: plain, 3: TMA ring, 4: flat stream
     uint32_t *d_status = nullptr;   // set by kernels whose bounded waits ran out
     int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
     int num_sms = 152;
@@ -306,7 +306,7 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     h->pf_ahead = o.slab_prefetch > 0 ? (int32_t)std::min<int64_t>(o.slab_prefetch, 1 << 20) : 0;
     h->pf_ahead = (h->pf_ahead + 255) / 256 * 256;
     h->loop_mode = o.loop_mode == 1 ? 1 : 0;
-    h->kernel = (o.kernel >= 0 && o.kernel <= 3) ? o.kernel : 0;
+    h->kernel = (o.kernel >= 0 && o.kernel <= 4) ? o.kernel : 0;
     if (o.x_stage_cols < 0 && h->kernel <= 1) h->kernel = 2;   // no shared-memory staging at all
     CK(cudaMalloc((void **)&h->d_status, sizeof(uint32_t)));
     CK(cudaMemset(h->d_status, 0, sizeof(uint32_t)));
@@ -675,6 +675,7 @@ static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
         } else if (staged && width >= 1024 && ph.nwl_total > 0) {
             pv.xs_cols = (int32_t)std::min<int64_t>(h->stage_cols, width);
             pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
+            pv.flat = h->kernel == 4 ? 1 : 0;
         } else {
             pv.xs_cols = 0;
             pv.nblocks = (int32_t)((ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);

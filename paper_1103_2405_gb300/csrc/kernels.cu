@@ -12,6 +12,7 @@
 // chunk to finish, summing the chunk partials in chunk order (deterministic).
 // No tensor cores: the gather is not a dense contraction.
 #include <atomic>
+#include <climits>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -35,6 +36,12 @@ constexpr int kPartMinBlocks = SPG_PART_MINB;
 // Staged variant: one 32-warp block per SM sharing up to kStagedMaxCols
 // floats (192 KB) of x in shared memory.
 constexpr int kStagedBlock = 1024;
+// Flat-stream variant: fewer warps with more registers each (B slots and B
+// gathers in flight per lane).
+#ifndef SPG_FLAT_BLOCK
+#define SPG_FLAT_BLOCK 768
+#endif
+constexpr int kFlatBlock = SPG_FLAT_BLOCK;
 
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -49,6 +56,26 @@ __device__ __forceinline__ double warp_sum_d(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
+
+// Per-thread running sum of the epilogue terms (L1 change, dangling mass,
+// HITS norms) as an unevaluated float pair s + c, each step Knuth's
+// TwoSum: the rounding error of s + a is carried in c.  Accurate to about
+// 2^-44 relative over the few thousand terms a thread adds, i.e. as good as
+// an FP64 running sum here, in FP32 arithmetic: GB300's FP64 rate is a small
+// fraction of its FP32 rate, and per-row FP64 adds and conversions were a
+// visible part of the epilogue time.  Converted to FP64 once per thread for
+// the warp / block reductions.
+struct FSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a)
+    {
+        const float t = s + a;
+        const float bp = t - s;
+        c += (s - (t - bp)) + (a - bp);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
 
 // One stored slot: padding has col = -1 and contributes nothing (no gather).
 __device__ __forceinline__ float slot_fma(uint2 v, const float *__restrict__ x, float acc)
@@ -110,7 +137,7 @@ __device__ __forceinline__ Epi load_epi(const IterState *st)
 template <int MODE>
 __device__ __forceinline__ void epilogue(const Epi &E, uint32_t rid, float tot,
                                          const float *__restrict__ x, float *__restrict__ y,
-                                         double &r0, double &r1)
+                                         FSum &r0, FSum &r1)
 {
     const uint32_t v = rid & kRowIdMask;
     if (rid & kRowNotFirst) tot += y[v];
@@ -122,8 +149,8 @@ __device__ __forceinline__ void epilogue(const Epi &E, uint32_t rid, float tot,
         float f = fmaf(E.c, tot, add);
         y[v] = f;
         if (MODE == EPI_PR_PAT) E.znew[v] = f * __ldg(E.invdeg + v);
-        r0 += fabs((double)f - (double)x[v]);
-        if ((int64_t)v >= E.dstart) r1 += (double)f;
+        r0.add(fabsf(f - x[v]));
+        if ((int64_t)v >= E.dstart) r1.add(f);
     } else if (MODE == EPI_BATCH) {
         y[v] = fmaf(E.c, tot, __ldg(E.gbase + __ldg(E.gid + v)));
     } else if (MODE == EPI_ADJ) {
@@ -132,13 +159,13 @@ __device__ __forceinline__ void epilogue(const Epi &E, uint32_t rid, float tot,
         const float add = (rid & kRowClass) ? E.c * x[E.seed] : 0.f;
         const float f = fmaf(E.c, tot, add + __ldg(E.aux + v));
         y[v] = f;
-        r0 += fabs((double)f - (double)x[v]);
+        r0.add(fabsf(f - x[v]));
     } else {  // HITS: a-rows read the hub half and vice versa
         const int cls = (rid & kRowClass) ? 1 : 0;
         float f = tot * (cls ? E.sc[0] : E.sc[1]);
         y[v] = f;
-        double q = E.hnorm == 2 ? (double)f * (double)f : (double)f;
-        if (cls == 0) r0 += q; else r1 += q;
+        const float q = E.hnorm == 2 ? f * f : f;
+        if (cls == 0) r0.add(q); else r1.add(q);
     }
 }
 
@@ -160,16 +187,16 @@ __device__ __noinline__ void finish_split(const Epi &E, const SplitView &sv, dou
     float tot = 0.f;
     for (int k = 0; k < sr.nchunks; ++k) tot += __ldcg(sv.partial + sr.first_slot + k);
     sv.counter[s] = 0u;
-    double r0 = 0.0, r1 = 0.0;
+    FSum r0, r1;
     epilogue<MODE>(E, sr.row, tot, x, y, r0, r1);
     if (MODE != EPI_RAW && MODE != EPI_RAW_PAT && MODE != EPI_BATCH)
-        red[sv.red_split_base + sr.red_slot] = make_double2(r0, r1);
+        red[sv.red_split_base + sr.red_slot] = make_double2(r0.value(), r1.value());
 }
 
 template <int MODE>
 __device__ __forceinline__ void finish_row(const Epi &E, const SplitView &sv, double2 *red,
                                            uint32_t rid, float acc, const float *__restrict__ x,
-                                           float *__restrict__ y, double &r0, double &r1)
+                                           float *__restrict__ y, FSum &r0, FSum &r1)
 {
     if (rid & kRowSplit) finish_split<MODE>(E, sv, red, rid, acc, x, y);
     else epilogue<MODE>(E, rid, acc, x, y, r0, r1);
@@ -218,7 +245,7 @@ __device__ __forceinline__ RowPre shfl_row(const RowPre &p, int src)
 // arithmetic as epilogue()).
 template <int MODE>
 __device__ __forceinline__ void epilogue_pre(const Epi &E, const RowPre &p, float tot,
-                                             float *__restrict__ y, double &r0, double &r1)
+                                             float *__restrict__ y, FSum &r0, FSum &r1)
 {
     const uint32_t rid = p.rid, v = rid & kRowIdMask;
     if (rid & kRowNotFirst) tot += p.yv;
@@ -230,21 +257,21 @@ __device__ __forceinline__ void epilogue_pre(const Epi &E, const RowPre &p, floa
         float f = fmaf(E.c, tot, add);
         y[v] = f;
         if (MODE == EPI_PR_PAT) E.znew[v] = f * p.av;
-        r0 += fabs((double)f - (double)p.xv);
-        if ((int64_t)v >= E.dstart) r1 += (double)f;
+        r0.add(fabsf(f - p.xv));
+        if ((int64_t)v >= E.dstart) r1.add(f);
     } else if (MODE == EPI_BATCH) {
         y[v] = fmaf(E.c, tot, p.av);
     } else if (MODE == EPI_ADJ) {
         const float add = (rid & kRowClass) ? E.c * E.xs : 0.f;
         const float f = fmaf(E.c, tot, add + p.av);
         y[v] = f;
-        r0 += fabs((double)f - (double)p.xv);
+        r0.add(fabsf(f - p.xv));
     } else {
         const int cls = (rid & kRowClass) ? 1 : 0;
         float f = tot * (cls ? E.sc[0] : E.sc[1]);
         y[v] = f;
-        double q = E.hnorm == 2 ? (double)f * (double)f : (double)f;
-        if (cls == 0) r0 += q; else r1 += q;
+        const float q = E.hnorm == 2 ? f * f : f;
+        if (cls == 0) r0.add(q); else r1.add(q);
     }
 }
 
@@ -252,15 +279,16 @@ template <int MODE>
 __device__ __forceinline__ void finish_row_pre(const Epi &E, const SplitView &sv, double2 *red,
                                                const RowPre &p, float acc,
                                                const float *__restrict__ x, float *__restrict__ y,
-                                               double &r0, double &r1)
+                                               FSum &r0, FSum &r1)
 {
     if (p.rid & kRowSplit) finish_split<MODE>(E, sv, red, p.rid, acc, x, y);
     else epilogue_pre<MODE>(E, p, acc, y, r0, r1);
 }
 
 template <int MODE>
-__device__ __forceinline__ void block_reduce_store(double r0, double r1, double2 *out)
+__device__ __forceinline__ void block_reduce_store(const FSum &f0, const FSum &f1, double2 *out)
 {
+    double r0 = f0.value(), r1 = f1.value();
     __shared__ double s0[32], s1[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     r0 = warp_sum_d(r0);
@@ -329,7 +357,7 @@ struct SlabPrefetch {
 // bytes) and every slot's value is 1 -- the column's value is folded into
 // the gathered vector (z = p * inv_deg for PageRank).  Both hand back a
 // {column, float bits} pair, padding as column -1.
-constexpr bool is_pattern(int mode) { return mode == EPI_PR_PAT || mode == EPI_RAW_PAT; }
+__host__ __device__ constexpr bool is_pattern(int mode) { return mode == EPI_PR_PAT || mode == EPI_RAW_PAT; }
 
 template <bool PAT> struct Slots;
 template <> struct Slots<false> {
@@ -352,7 +380,7 @@ template <int MODE, class G>
 __device__ __forceinline__ void do_workload(const Workload &d, const PartView &pv,
                                             const SplitView &sv, const G &g, const Epi &E,
                                             const float *__restrict__ x, float *__restrict__ y,
-                                            double2 *red, int lane, double &r0, double &r1)
+                                            double2 *red, int lane, FSum &r0, FSum &r1)
 {
     const uint32_t *__restrict__ rows = pv.rows + d.rows;
     const Slots<is_pattern(MODE)> slab{pv, d.slab};
@@ -458,6 +486,88 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
     }
 }
 
+// Flat-stream variant of do_workload (kernel option 4).  The warp walks
+// its workload as one sequence of 32-slot steps -- row after row for a
+// row-major workload, column after column of each 32-row block for a
+// column-major one -- in batches of B steps: the gathers of a batch are
+// issued, then the loads of the next batch, then the batch is summed.  The
+// slot loads therefore stay in flight across row boundaries (no drain at the
+// end of every row) and every lane keeps B slots and B gathers outstanding.
+// Row-major rows end on step boundaries (w is a multiple of 32); the
+// warp-uniform test `t + u + 1 == rend` finishes a row inside a batch.
+template <int MODE, class G>
+__device__ __forceinline__ void do_workload_flat(const Workload &d, const PartView &pv,
+                                                 const SplitView &sv, const G &g, const Epi &E,
+                                                 const float *__restrict__ x, float *__restrict__ y,
+                                                 double2 *red, int lane, FSum &r0, FSum &r1)
+{
+    constexpr int B = is_pattern(MODE) ? 16 : 8;
+    const uint2 pad = make_uint2(0xffffffffu, 0u);
+    const uint32_t *__restrict__ rows = pv.rows + d.rows;
+    const Slots<is_pattern(MODE)> slab{pv, d.slab};
+    if (d.major == 0) {
+        const int nst = d.w >> 5;
+        const int T = d.h * nst;
+        uint2 a[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) a[u] = u < T ? slab.ld((int64_t)u * 32 + lane) : pad;
+        RowPre mine = prefetch_row<MODE>(E, rows, lane, lane < d.h, x, y);
+        int r = 0, rend = nst;
+        float acc = 0.f;
+        for (int t = 0; t < T; t += B) {
+            float xv[B], vv[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int c = (int)a[u].x;
+                xv[u] = c >= 0 ? g(c) : 0.f;
+                vv[u] = __uint_as_float(a[u].y);
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                a[u] = t + B + u < T ? slab.ld((int64_t)(t + B + u) * 32 + lane) : pad;
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                acc = fmaf(vv[u], xv[u], acc);
+                if (t + u + 1 == rend) {
+                    const float tot = warp_sum(acc);
+                    const RowPre p = shfl_row(mine, r & 31);
+                    if (lane == 0) finish_row_pre<MODE>(E, sv, red, p, tot, x, y, r0, r1);
+                    acc = 0.f;
+                    ++r;
+                    rend = r < d.h ? rend + nst : INT_MAX;
+                    if ((r & 31) == 0 && r < d.h)
+                        mine = prefetch_row<MODE>(E, rows, r + lane, r + lane < d.h, x, y);
+                }
+            }
+        }
+    } else {
+        const int hp = (d.h + 31) & ~31;
+        for (int b = 0; b < hp; b += 32) {
+            const RowPre p = prefetch_row<MODE>(E, rows, b + lane, b + lane < d.h, x, y);
+            const int64_t s0 = (int64_t)b * d.w + lane;
+            uint2 a[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) a[u] = u < d.w ? slab.ld(s0 + (int64_t)u * 32) : pad;
+            float acc = 0.f;
+            for (int e = 0; e < d.w; e += B) {
+                float xv[B], vv[B];
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const int c = (int)a[u].x;
+                    xv[u] = c >= 0 ? g(c) : 0.f;
+                    vv[u] = __uint_as_float(a[u].y);
+                }
+#pragma unroll
+                for (int u = 0; u < B; ++u)
+                    a[u] = e + B + u < d.w ? slab.ld(s0 + (int64_t)(e + B + u) * 32) : pad;
+#pragma unroll
+                for (int u = 0; u < B; ++u) acc = fmaf(vv[u], xv[u], acc);
+            }
+            if (b + lane < d.h) finish_row_pre<MODE>(E, sv, red, p, acc, x, y, r0, r1);
+        }
+    }
+}
+
 template <int MODE>
 __device__ __forceinline__ void resolve_xy(const IterState *st, const float *&x, float *&y)
 {
@@ -483,7 +593,7 @@ k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restri
     const float *gsrc = (MODE == EPI_PR_PAT) ? st->zbuf[st->parity] : x;
     const int lane = threadIdx.x & 31;
     const int wid = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    double r0 = 0.0, r1 = 0.0;
+    FSum r0, r1;
     if (wid < pv.nwl) {
         const GatherGlobal g{gsrc};
         do_workload<MODE>(pv.wl[wid], pv, sv, g, E, x, y, red, lane, r0, r1);
@@ -498,8 +608,8 @@ k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restri
 // Section 3.1 Solution 1), then its warps take workloads in order from a
 // counter (pv.sched[0]); the last warp out resets the counters for the next
 // launch (pv.sched[1] counts finished warps).  No waits between blocks.
-template <int MODE>
-__global__ void __launch_bounds__(kStagedBlock, 1)
+template <int MODE, bool FLAT>
+__global__ void __launch_bounds__(FLAT ? kFlatBlock : kStagedBlock, 1)
 k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
               float *__restrict__ yout, const IterState *__restrict__ st,
               double2 *__restrict__ red)
@@ -522,13 +632,14 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
     __syncthreads();
     const GatherStaged g{gsrc, xs, c0, (unsigned)S};
     const int lane = threadIdx.x & 31;
-    double r0 = 0.0, r1 = 0.0;
+    FSum r0, r1;
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(pv.sched, 1u);
         w = __shfl_sync(kFull, w, 0);
         if (w >= (unsigned)pv.nwl) break;
-        do_workload<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, r0, r1);
+        if (FLAT) do_workload_flat<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, r0, r1);
+        else do_workload<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, r0, r1);
     }
     if (lane == 0) {
         const unsigned done = atomicAdd(pv.sched + 1, 1u);
@@ -620,7 +731,7 @@ __device__ __forceinline__ void do_workload_tma(const Workload &d, const PartVie
                                                 const SplitView &sv, const G &g, const Epi &E,
                                                 const float *__restrict__ x,
                                                 float *__restrict__ y, double2 *red, int lane,
-                                                TmaRing &R, double &r0, double &r1)
+                                                TmaRing &R, FSum &r0, FSum &r1)
 {
     const uint32_t *__restrict__ rows = pv.rows + d.rows;
     const int hp = d.major == 0 ? d.h : (d.h + 31) & ~31;
@@ -719,7 +830,7 @@ k_part_tma(PartView pv, SplitView sv, const float *__restrict__ xin, float *__re
     }
     __syncthreads();
     const GatherStaged g{x, xs, c0, (unsigned)S};
-    double r0 = 0.0, r1 = 0.0;
+    FSum r0, r1;
     for (;;) {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(pv.sched, 1u);
@@ -769,12 +880,17 @@ template <int MODE> static void launch_staged(const PartView &pv, const SplitVie
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_part_staged<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_part_staged<MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kStagedMaxCols * (int)sizeof(float));
+        cudaFuncSetAttribute(k_part_staged<MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kStagedMaxCols * (int)sizeof(float));
         attr = true;
     }
-    k_part_staged<MODE><<<pv.nblocks, kStagedBlock, (size_t)pv.xs_cols * sizeof(float), s>>>(
-        pv, sv, x, y, st, red);
+    const size_t smem = (size_t)pv.xs_cols * sizeof(float);
+    if (pv.flat)
+        k_part_staged<MODE, true><<<pv.nblocks, kFlatBlock, smem, s>>>(pv, sv, x, y, st, red);
+    else
+        k_part_staged<MODE, false><<<pv.nblocks, kStagedBlock, smem, s>>>(pv, sv, x, y, st, red);
 }
 
 void launch_part(int mode, const PartView &pv, const SplitView &sv, const float *x, float *y,
@@ -893,7 +1009,7 @@ template <int MODE>
 __device__ __forceinline__ void epilogue_k(const EpiK &E, uint32_t rid, float t0, float t1,
                                            int j0, int k, const float *__restrict__ X,
                                            float *__restrict__ Y, const int32_t *seeds,
-                                           const double *delta_k, double *acc4)
+                                           const double *delta_k, FSum *acc4)
 {
     const uint32_t v = rid & kRowIdMask;
     float *yr = Y + (int64_t)v * k;
@@ -910,15 +1026,15 @@ __device__ __forceinline__ void epilogue_k(const EpiK &E, uint32_t rid, float t0
         float add = (int)v == __ldg(seeds + j0) ? (float)(c * delta_k[j0] + (1.0 - c)) : 0.f;
         float f = fmaf(E.c, t0, add);
         yr[j0] = f;
-        acc4[0] += fabs((double)f - (double)xr[j0]);
-        if ((int64_t)v >= E.dstart) acc4[2] += f;
+        acc4[0].add(fabsf(f - xr[j0]));
+        if ((int64_t)v >= E.dstart) acc4[2].add(f);
     }
     if (h1) {
         float add = (int)v == __ldg(seeds + j0 + 1) ? (float)(c * delta_k[j0 + 1] + (1.0 - c)) : 0.f;
         float f = fmaf(E.c, t1, add);
         yr[j0 + 1] = f;
-        acc4[1] += fabs((double)f - (double)xr[j0 + 1]);
-        if ((int64_t)v >= E.dstart) acc4[3] += f;
+        acc4[1].add(fabsf(f - xr[j0 + 1]));
+        if ((int64_t)v >= E.dstart) acc4[3].add(f);
     }
 }
 
@@ -945,7 +1061,7 @@ k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__r
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wid = blockIdx.x * kWarpsPerBlock + warp;
-    double acc4[4] = {0.0, 0.0, 0.0, 0.0};   // L1 j0, L1 j0+1, dangling j0, dangling j0+1
+    FSum acc4[4];   // L1 j0, L1 j0+1, dangling j0, dangling j0+1
     if (wid < pv.nwl) {
         const Workload d = pv.wl[wid];
         const uint2 *slab = pv.slab + d.slab;
@@ -970,7 +1086,7 @@ k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__r
                     prev = __shfl_sync(kFull, prev, 0);
                     if (prev != (unsigned)sr.nchunks - 1) continue;
                     __threadfence();
-                    double sr4[4] = {0.0, 0.0, 0.0, 0.0};
+                    FSum sr4[4];
                     for (int cc = 0; cc < k; cc += 64) {
                         const int jj = cc + 2 * lane;
                         float t0 = 0.f, t1 = 0.f;
@@ -984,9 +1100,9 @@ k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__r
                     if (lane == 0) sv.counter[s] = 0u;
                     if (MODE != EPI_RAW && j0 < k) {
                         double *o = redk + (int64_t)(sv.red_split_base + sr.red_slot) * 2 * k;
-                        o[j0] = sr4[0];
-                        o[k + j0] = sr4[2];
-                        if (j0 + 1 < k) { o[j0 + 1] = sr4[1]; o[k + j0 + 1] = sr4[3]; }
+                        o[j0] = sr4[0].value();
+                        o[k + j0] = sr4[2].value();
+                        if (j0 + 1 < k) { o[j0 + 1] = sr4[1].value(); o[k + j0 + 1] = sr4[3].value(); }
                     }
                 } else {
                     epilogue_k<MODE>(E, rid, a0, a1, j0, k, X, Y, seeds, delta_k, acc4);
@@ -997,8 +1113,8 @@ k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__r
     if (MODE != EPI_RAW) {
         // per-block column sums (k <= 64 for the RWR epilogue)
         __shared__ double sm[kWarpsPerBlock][4][32];
-        sm[warp][0][lane] = acc4[0]; sm[warp][1][lane] = acc4[1];
-        sm[warp][2][lane] = acc4[2]; sm[warp][3][lane] = acc4[3];
+        sm[warp][0][lane] = acc4[0].value(); sm[warp][1][lane] = acc4[1].value();
+        sm[warp][2][lane] = acc4[2].value(); sm[warp][3][lane] = acc4[3].value();
         __syncthreads();
         if (threadIdx.x < 128) {
             const int q = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -1022,7 +1138,7 @@ template <int MODE>
 __device__ __forceinline__ void epilogue_k64(float c, int64_t dstart, uint32_t rid, float4 t,
                                              int j0, const float *__restrict__ X,
                                              float *__restrict__ Y, const int32_t *seeds,
-                                             const double *delta_k, double *acc8)
+                                             const double *delta_k, FSum *acc8)
 {
     const uint32_t v = rid & kRowIdMask;
     float4 *yr = reinterpret_cast<float4 *>(Y + (int64_t)v * 64 + j0);
@@ -1038,8 +1154,8 @@ __device__ __forceinline__ void epilogue_k64(float c, int64_t dstart, uint32_t r
         const int j = j0 + q;
         const float add = (int)v == __ldg(seeds + j) ? (float)((double)c * delta_k[j] + (1.0 - (double)c)) : 0.f;
         f[q] = fmaf(c, tt[q], add);
-        acc8[q] += fabs((double)f[q] - (double)xx[q]);
-        if ((int64_t)v >= dstart) acc8[4 + q] += (double)f[q];
+        acc8[q].add(fabsf(f[q] - xx[q]));
+        if ((int64_t)v >= dstart) acc8[4 + q].add(f[q]);
     }
     *yr = make_float4(f[0], f[1], f[2], f[3]);
 }
@@ -1066,7 +1182,7 @@ k_part_spmm64(PartView pv, SplitView sv, const float *__restrict__ Xin, float *_
     const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
     const int j0 = 4 * hl;
     const int wid = blockIdx.x * kWarpsPerBlock + warp;
-    double acc8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    FSum acc8[8];
     if (wid < pv.nwl) {
         const Workload d = pv.wl[wid];
         const uint2 *slab = pv.slab + d.slab;
@@ -1120,13 +1236,13 @@ k_part_spmm64(PartView pv, SplitView sv, const float *__restrict__ Xin, float *_
                         sv.partial + (int64_t)(sr.first_slot + q) * 64 + j0));
                     tot.x += pq.x; tot.y += pq.y; tot.z += pq.z; tot.w += pq.w;
                 }
-                double s8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                FSum s8[8];
                 epilogue_k64<MODE>(c, dstart, sr.row, tot, j0, X, Y, seeds, delta_k, s8);
                 if (hl == 0) sv.counter[s] = 0u;
                 if (MODE != EPI_RAW) {
                     double *o = redk + (int64_t)(sv.red_split_base + sr.red_slot) * 128;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) { o[j0 + q] = s8[q]; o[64 + j0 + q] = s8[4 + q]; }
+                    for (int q = 0; q < 4; ++q) { o[j0 + q] = s8[q].value(); o[64 + j0 + q] = s8[4 + q].value(); }
                 }
             } else {
                 epilogue_k64<MODE>(c, dstart, rid, a, j0, X, Y, seeds, delta_k, acc8);
@@ -1136,11 +1252,15 @@ k_part_spmm64(PartView pv, SplitView sv, const float *__restrict__ Xin, float *_
     if (MODE != EPI_RAW) {
         // both halves hold the same 4 columns: add them, then warps in order
         __shared__ double sm[kWarpsPerBlock][16][8];
+        double a8[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc8[q] += __shfl_xor_sync(kFull, acc8[q], 16);
+        for (int q = 0; q < 8; ++q) {
+            a8[q] = acc8[q].value();
+            a8[q] += __shfl_xor_sync(kFull, a8[q], 16);
+        }
         if (half == 0) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) sm[warp][hl][q] = acc8[q];
+            for (int q = 0; q < 8; ++q) sm[warp][hl][q] = a8[q];
         }
         __syncthreads();
         if (threadIdx.x < 128) {
@@ -1374,16 +1494,16 @@ __global__ void __launch_bounds__(256) k_batch_reduce(IterState *st)
     const float *x = st->buf[st->parity];
     const float *y = st->buf[st->parity ^ 1];
     const int64_t a = st->goff[g], b = st->goff[g + 1], ds = st->gdstart[g];
-    double l1 = 0.0, dg = 0.0;
+    FSum fl1, fdg;
     for (int64_t v = a + threadIdx.x; v < b; v += blockDim.x) {
         const float f = y[v];
-        l1 += fabs((double)f - (double)x[v]);
-        if (v >= ds) dg += (double)f;
+        fl1.add(fabsf(f - x[v]));
+        if (v >= ds) fdg.add(f);
     }
     __shared__ double s0[8], s1[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    l1 = warp_sum_d(l1);
-    dg = warp_sum_d(dg);
+    const double l1 = warp_sum_d(fl1.value());
+    const double dg = warp_sum_d(fdg.value());
     if (lane == 0) { s0[warp] = l1; s1[warp] = dg; }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1633,13 +1753,13 @@ void launch_onehot_rows(int64_t n, int k, const int32_t *seeds, float *X, cudaSt
 template <int MODE>
 __device__ __forceinline__ void csr_epilogue(const Epi &E, int64_t v, float acc,
                                              const uint8_t *dangling, const float *x, float *y,
-                                             double &r0, double &r1)
+                                             FSum &r0, FSum &r1)
 {
     if (MODE == EPI_RAW) { y[v] = acc; return; }
     const float f = fmaf(E.c, acc, E.base);
     y[v] = f;
-    r0 += fabs((double)f - (double)x[v]);
-    if (dangling[v]) r1 += (double)f;
+    r0.add(fabsf(f - x[v]));
+    if (dangling[v]) r1.add(f);
 }
 
 // Appendix B CSR kernel: one thread per row.
@@ -1655,7 +1775,7 @@ k_csr_scalar(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restric
     Epi E = load_epi<MODE>(st);
     if (st) { x = st->buf[st->parity]; y = st->buf[st->parity ^ 1]; }
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double r0 = 0.0, r1 = 0.0;
+    FSum r0, r1;
     if (v < n) {
         float acc = 0.f;
         for (int64_t k = rp[v]; k < rp[v + 1]; ++k) acc = fmaf(val[k], __ldg(x + col[k]), acc);
@@ -1678,7 +1798,7 @@ k_csr_vector(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restric
     if (st) { x = st->buf[st->parity]; y = st->buf[st->parity ^ 1]; }
     const int lane = threadIdx.x & 31;
     const int64_t v = blockIdx.x * (int64_t)kWarpsPerBlock + (threadIdx.x >> 5);
-    double r0 = 0.0, r1 = 0.0;
+    FSum r0, r1;
     if (v < n) {
         float acc = 0.f;
         for (int64_t k = rp[v] + lane; k < rp[v + 1]; k += 32) acc = fmaf(val[k], __ldg(x + col[k]), acc);

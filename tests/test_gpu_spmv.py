@@ -32,6 +32,13 @@ def _graph(kind):
         return np.zeros(101, np.int64), np.zeros(0, np.int32)
     if kind == "single":
         return np.zeros(2, np.int64), np.zeros(0, np.int32)
+    if kind == "varied":    # 2048 nodes, in-degrees spread over 0..1500: rows of every length
+        rng = np.random.default_rng(11)
+        n = 2048
+        deg = rng.integers(0, 1501, size=n)
+        dst = np.repeat(np.arange(n), deg)
+        src = rng.integers(0, n, size=dst.shape[0])
+        return graphgen.edges_to_csr(n, src, dst)
     if kind == "dense":     # dense 300 x 300 (every off-diagonal edge)
         n = 300
         u, v = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
@@ -55,6 +62,13 @@ CONFIGS = [
     ("hub", dict(pattern_only=True)),
     ("rmat14", dict(kernel=2)),                                # plain 8-warp kernel
     ("rmat14", dict(kernel=3, tile_width=2048)),               # TMA ring kernel
+    ("rmat14", dict(kernel=4)),                                # flat-stream kernel
+    ("rmat14", dict(kernel=4, tile_width=2048, pattern_only=True)),
+    ("varied", dict(kernel=4)),
+    ("varied", dict(kernel=4, heavy_row=256, max_rows=-1)),
+    ("varied", dict(kernel=4, pattern_only=True, max_rows=100)),
+    ("varied", dict()),
+    ("hub", dict(kernel=4)),
     ("rmat14", dict(tile_width=2048)),                         # dense tiles + sparse tail
     ("rmat14", dict(tile_width=256, heavy_row=0)),             # no split rows
     ("rmat14", dict(tile_width=4096, heavy_row=32, layout_rule=0)),
