@@ -148,6 +148,27 @@ def batch_graphs(count=512):
             for g, n in enumerate(sizes)]
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
+# capture summarised under profiles/, keyed by workload, with the SHA-256 of
+# the kernel source the counters were taken on: reported only while that
+# source is unchanged (null otherwise).
+NCU_TRAFFIC = {}
+
+
+def kernel_source_sha():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1103_2405_gb300", "csrc", "kernels.cu")
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def ncu_traffic(workload):
+    rec = NCU_TRAFFIC.get(workload)
+    if rec is None or rec[1] != kernel_source_sha():
+        return None
+    return rec[0]
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -375,8 +396,10 @@ def main():
     alg_bytes = 8 * nnz + 4 * n + 4 * n + 4 * n + 4 * n
     k_ms = float(part_ms.sum())
     roofline = {"bound": "hbm", "achieved": alg_bytes / (k_ms * 1e-3) / 1e9, "peak": peak,
-                "unit": "GB/s", "frac": alg_bytes / (k_ms * 1e-3) / 1e9 / peak, "traffic": None,
-                "kernel": "k_part<EPI_PAGERANK>", "kernel_ms": k_ms,
+                "unit": "GB/s", "frac": alg_bytes / (k_ms * 1e-3) / 1e9 / peak,
+                "traffic": ncu_traffic(args.workload),
+                "kernel": "k_part_staged<EPI_PAGERANK> (fused PageRank SpMV, one launch per part)",
+                "kernel_ms": k_ms,
                 "alg_bytes_per_launch": alg_bytes,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800"}
 
