@@ -938,70 +938,43 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
 }
 
 // ------------------------------------------------------------------ SpMM --
+//
+// Y' = M' X' for k vectors (X' n x k row-major).  One warp per workload, the
+// k columns in chunks of 64: lane l owns columns c0 + 2l and c0 + 2l + 1, so
+// every stored entry (c, v) costs one coalesced gather of 64 columns of X
+// row c (256 bytes per warp) and two FMAs per lane.  The gather is the
+// dominant traffic (4k bytes per entry against 8 for the slot), so the
+// kernel keeps kSpmmU entries' gathers in flight per lane:
+// * row-major workload: a batch of 32 entries of the row is loaded one per
+//   lane and broadcast by shuffles, kSpmmU at a time; the next batch's slots
+//   are loaded before the current batch is consumed;
+// * column-major block of 32 rows: step e holds entry e of all 32 rows, so
+//   the warp keeps the 32 rows' partial sums in registers (acc[32], static
+//   indices) and walks the block step by step -- short rows cost no
+//   per-row latency chain.
+// The epilogue (split rows, RWR terms, per-column sums) is per row with one
+// lane per column pair.
 
-// Y' row v, columns [c0, c0+64) of one chunk: lane owns columns c0+2*lane,
-// c0+2*lane+1.  The row's stored entries are a prefix of its slots (padding
-// last), so a batch of 32 entries is loaded one per lane and broadcast.
-__device__ __forceinline__ uint2 ld_entry(const uint2 *slab, const Workload &d, int i, int e)
-{
-    const int64_t off = d.major == 0 ? (int64_t)i * d.w + e
-                                     : (int64_t)(i >> 5) * 32 * d.w + (int64_t)e * 32 + (i & 31);
-    return __ldcs(slab + off);
-}
-
-template <bool EVEN>
-__device__ __forceinline__ void row_spmm(const uint2 *slab, const Workload &d, int i,
-                                         const float *__restrict__ X, int k, int j0, int lane,
-                                         float &a0, float &a1)
-{
-    const int wrow = d.major == 0 ? d.w : d.w;  // entries stored per row
-    for (int e0 = 0; e0 < wrow; e0 += 32) {
-        const int e = e0 + lane;
-        uint2 ent = make_uint2(0xffffffffu, 0u);
-        if (e < wrow) ent = ld_entry(slab, d, i, e);
-        const unsigned valid = __ballot_sync(kFull, (int)ent.x >= 0);
-        const int cnt = __popc(valid);
-        int t = 0;
-        for (; t + 1 < cnt; t += 2) {
-            const int c_0 = __shfl_sync(kFull, (int)ent.x, t);
-            const float v_0 = __shfl_sync(kFull, __uint_as_float(ent.y), t);
-            const int c_1 = __shfl_sync(kFull, (int)ent.x, t + 1);
-            const float v_1 = __shfl_sync(kFull, __uint_as_float(ent.y), t + 1);
-            const float *r0p = X + (int64_t)c_0 * k, *r1p = X + (int64_t)c_1 * k;
-            if (EVEN) {
-                if (j0 < k) {
-                    const float2 p = __ldg(reinterpret_cast<const float2 *>(r0p + j0));
-                    const float2 q = __ldg(reinterpret_cast<const float2 *>(r1p + j0));
-                    a0 = fmaf(v_0, p.x, a0); a1 = fmaf(v_0, p.y, a1);
-                    a0 = fmaf(v_1, q.x, a0); a1 = fmaf(v_1, q.y, a1);
-                }
-            } else {
-                if (j0 < k) { a0 = fmaf(v_0, __ldg(r0p + j0), a0); a0 = fmaf(v_1, __ldg(r1p + j0), a0); }
-                if (j0 + 1 < k) { a1 = fmaf(v_0, __ldg(r0p + j0 + 1), a1); a1 = fmaf(v_1, __ldg(r1p + j0 + 1), a1); }
-            }
-        }
-        for (; t < cnt; ++t) {
-            const int c_0 = __shfl_sync(kFull, (int)ent.x, t);
-            const float v_0 = __shfl_sync(kFull, __uint_as_float(ent.y), t);
-            const float *r0p = X + (int64_t)c_0 * k;
-            if (EVEN) {
-                if (j0 < k) {
-                    const float2 p = __ldg(reinterpret_cast<const float2 *>(r0p + j0));
-                    a0 = fmaf(v_0, p.x, a0); a1 = fmaf(v_0, p.y, a1);
-                }
-            } else {
-                if (j0 < k) a0 = fmaf(v_0, __ldg(r0p + j0), a0);
-                if (j0 + 1 < k) a1 = fmaf(v_0, __ldg(r0p + j0 + 1), a1);
-            }
-        }
-        if (cnt < 32) break;
-    }
-}
+constexpr int kSpmmU = 8;
+constexpr size_t kSpmmTileBytes = (size_t)kWarpsPerBlock * 32 * 32 * sizeof(float2);   // 64 KB
 
 struct EpiK {
     float c;
     int64_t dstart;
 };
+
+// One stored entry's gather: X row c, the lane's two columns.
+template <bool EVEN>
+__device__ __forceinline__ float2 gather2(const float *__restrict__ X, int c, int k, int j0)
+{
+    float2 p = make_float2(0.f, 0.f);
+    if (c < 0 || j0 >= k) return p;
+    const float *r = X + (int64_t)c * k + j0;
+    if (EVEN) return __ldg(reinterpret_cast<const float2 *>(r));
+    p.x = __ldg(r);
+    if (j0 + 1 < k) p.y = __ldg(r + 1);
+    return p;
+}
 
 // Row epilogue for SpMM: RAW or RWR per column (restart seeds[j], dangling
 // mass delta_k[j]).  Per-lane sums for its two columns.
@@ -1038,11 +1011,179 @@ __device__ __forceinline__ void epilogue_k(const EpiK &E, uint32_t rid, float t0
     }
 }
 
+// A finished row (chunk c0 of its columns) of the SpMM: either the epilogue,
+// or -- for a chunk of a split row -- publish the partial; after the last
+// column chunk the last chunk of the row to arrive sums all partials in chunk
+// order and runs the epilogue for every column chunk.  Warp-uniform.
+template <int MODE>
+__device__ __noinline__ void spmm_finish_split(const EpiK &E, const SplitView &sv, uint32_t rid,
+                                               float a0, float a1, int c0, int k, int lane,
+                                               const float *__restrict__ X, float *__restrict__ Y,
+                                               const int32_t *seeds, const double *delta_k,
+                                               double *redk)
+{
+    const int j0 = c0 + 2 * lane;
+    const int slot = (int)(rid & 0x7fffffffu);
+    float *pp = sv.partial + (int64_t)slot * k;
+    if (j0 < k) pp[j0] = a0;
+    if (j0 + 1 < k) pp[j0 + 1] = a1;
+    if (c0 + 64 < k) return;   // publish after the last column chunk
+    __threadfence();
+    __syncwarp();
+    const int s = sv.slot_owner[slot];
+    const SplitRow sr = sv.rows[s];
+    unsigned prev = 0;
+    if (lane == 0) prev = atomicAdd(sv.counter + s, 1u);
+    prev = __shfl_sync(kFull, prev, 0);
+    if (prev != (unsigned)sr.nchunks - 1) return;
+    __threadfence();
+    FSum sr4[4];
+    for (int cc = 0; cc < k; cc += 64) {
+        const int jj = cc + 2 * lane;
+        float t0 = 0.f, t1 = 0.f;
+        for (int q = 0; q < sr.nchunks; ++q) {
+            const float *src = sv.partial + (int64_t)(sr.first_slot + q) * k;
+            if (jj < k) t0 += __ldcg(src + jj);
+            if (jj + 1 < k) t1 += __ldcg(src + jj + 1);
+        }
+        epilogue_k<MODE>(E, sr.row, t0, t1, jj, k, X, Y, seeds, delta_k, sr4);
+    }
+    if (lane == 0) sv.counter[s] = 0u;
+    if (MODE != EPI_RAW && j0 < k) {
+        double *o = redk + (int64_t)(sv.red_split_base + sr.red_slot) * 2 * k;
+        o[j0] = sr4[0].value();
+        o[k + j0] = sr4[2].value();
+        if (j0 + 1 < k) { o[j0 + 1] = sr4[1].value(); o[k + j0 + 1] = sr4[3].value(); }
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void spmm_finish(const EpiK &E, const SplitView &sv, uint32_t rid,
+                                            float a0, float a1, int c0, int k, int lane,
+                                            const float *__restrict__ X, float *__restrict__ Y,
+                                            const int32_t *seeds, const double *delta_k,
+                                            double *redk, FSum *acc4)
+{
+    if (rid & kRowSplit)
+        spmm_finish_split<MODE>(E, sv, rid, a0, a1, c0, k, lane, X, Y, seeds, delta_k, redk);
+    else
+        epilogue_k<MODE>(E, rid, a0, a1, c0 + 2 * lane, k, X, Y, seeds, delta_k, acc4);
+}
+
+// Row-major workload: rows one after another, 32 entries per batch.
+template <int MODE, bool EVEN>
+__device__ __forceinline__ void spmm_rows(const Workload &d, const uint2 *__restrict__ slab,
+                                          const uint32_t *__restrict__ rows, const EpiK &E,
+                                          const SplitView &sv, const float *__restrict__ X,
+                                          float *__restrict__ Y, int k, int lane,
+                                          const int32_t *seeds, const double *delta_k,
+                                          double *redk, FSum *acc4)
+{
+    const uint2 pad = make_uint2(0xffffffffu, 0u);
+    for (int c0 = 0; c0 < k; c0 += 64) {
+        const int j0 = c0 + 2 * lane;
+        for (int i = 0; i < d.h; ++i) {
+            const uint32_t rid = __ldg(rows + i);
+            const uint2 *rs = slab + (int64_t)i * d.w;
+            float a0 = 0.f, a1 = 0.f;
+            uint2 nxt = d.w > 0 ? __ldcs(rs + lane) : pad;
+            for (int e0 = 0; e0 < d.w; e0 += 32) {
+                const uint2 ent = nxt;
+                const int cnt = __popc(__ballot_sync(kFull, (int)ent.x >= 0));
+                // entries are a prefix of the row's slots: a full batch may
+                // have a successor, a partial one ends the row
+                nxt = (cnt == 32 && e0 + 32 < d.w) ? __ldcs(rs + e0 + 32 + lane) : pad;
+                for (int t = 0; t < cnt; t += kSpmmU) {
+                    float2 p[kSpmmU];
+                    float vv[kSpmmU];
+#pragma unroll
+                    for (int u = 0; u < kSpmmU; ++u) {
+                        const int c = __shfl_sync(kFull, (int)ent.x, (t + u) & 31);
+                        vv[u] = __shfl_sync(kFull, __uint_as_float(ent.y), (t + u) & 31);
+                        p[u] = gather2<EVEN>(X, t + u < cnt ? c : -1, k, j0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kSpmmU; ++u) {
+                        const float w = t + u < cnt ? vv[u] : 0.f;
+                        a0 = fmaf(w, p[u].x, a0);
+                        a1 = fmaf(w, p[u].y, a1);
+                    }
+                }
+                if (cnt < 32) break;
+            }
+            spmm_finish<MODE>(E, sv, rid, a0, a1, c0, k, lane, X, Y, seeds, delta_k, redk, acc4);
+        }
+    }
+}
+
+// Column-major workload: 32-row blocks, step e = entry e of each of the 32
+// rows (one slot per lane); the 32 rows' sums stay in registers.
+template <int MODE, bool EVEN>
+__device__ __forceinline__ void spmm_block(const Workload &d, const uint2 *__restrict__ slab,
+                                           const uint32_t *__restrict__ rows, const EpiK &E,
+                                           const SplitView &sv, const float *__restrict__ X,
+                                           float *__restrict__ Y, int k, int lane,
+                                           const int32_t *seeds, const double *delta_k,
+                                           double *redk, FSum *acc4, float2 *tile)
+{
+    const uint2 pad = make_uint2(0xffffffffu, 0u);
+    const int hp = (d.h + 31) & ~31;
+    for (int b = 0; b < hp; b += 32) {
+        const uint32_t my_rid = b + lane < d.h ? __ldg(rows + b + lane) : 0u;
+        const uint2 *blk = slab + (int64_t)b * d.w;
+        for (int c0 = 0; c0 < k; c0 += 64) {
+            const int j0 = c0 + 2 * lane;
+            float2 acc[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) acc[t] = make_float2(0.f, 0.f);
+            uint2 nxt = d.w > 0 ? __ldcs(blk + lane) : pad;
+            for (int e = 0; e < d.w; ++e) {
+                const uint2 ent = nxt;
+                nxt = e + 1 < d.w ? __ldcs(blk + (int64_t)(e + 1) * 32 + lane) : pad;
+#pragma unroll
+                for (int t0 = 0; t0 < 32; t0 += kSpmmU) {
+                    float2 p[kSpmmU];
+                    float vv[kSpmmU];
+#pragma unroll
+                    for (int u = 0; u < kSpmmU; ++u) {
+                        const int c = __shfl_sync(kFull, (int)ent.x, t0 + u);
+                        vv[u] = __shfl_sync(kFull, __uint_as_float(ent.y), t0 + u);
+                        p[u] = gather2<EVEN>(X, c, k, j0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kSpmmU; ++u) {
+                        acc[t0 + u].x = fmaf(vv[u], p[u].x, acc[t0 + u].x);
+                        acc[t0 + u].y = fmaf(vv[u], p[u].y, acc[t0 + u].y);
+                    }
+                }
+            }
+            // the epilogue reads the sums back row by row from the warp's
+            // shared-memory tile (one 64-column row per step, lane l holds
+            // columns 2l, 2l+1): a rolled loop, so the 32 sums are not live
+            // across 32 inlined epilogues
+#pragma unroll
+            for (int t = 0; t < 32; ++t) tile[t * 32 + lane] = acc[t];
+            __syncwarp();
+            const int nr = min(32, d.h - b);
+#pragma unroll 1
+            for (int t = 0; t < nr; ++t) {
+                const uint32_t rid = __shfl_sync(kFull, my_rid, t);
+                const float2 a = tile[t * 32 + lane];
+                spmm_finish<MODE>(E, sv, rid, a.x, a.y, c0, k, lane, X, Y, seeds, delta_k, redk, acc4);
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // SpMM over one part.  Split rows: chunk partials (k floats per chunk slot)
 // in sv.partial, combined in chunk order by the last chunk.  Per-block
 // column sums for RWR into redk[(slot * 2 + q) * k + j] (q = 0: L1, 1: dangling).
+#ifndef SPG_SPMM_MINB
+#define SPG_SPMM_MINB 2
+#endif
 template <int MODE, bool EVEN>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, SPG_SPMM_MINB)
 k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__restrict__ Yout,
             int k, const IterState *__restrict__ st, const int32_t *__restrict__ seeds,
             const double *__restrict__ delta_k, double *__restrict__ redk)
@@ -1059,56 +1200,19 @@ k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__r
         E.c = (float)st->c;
         E.dstart = st->dangling_start;
     }
+    extern __shared__ float2 spmm_tile[];   // per warp: 32 rows x 64 columns
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wid = blockIdx.x * kWarpsPerBlock + warp;
     FSum acc4[4];   // L1 j0, L1 j0+1, dangling j0, dangling j0+1
     if (wid < pv.nwl) {
         const Workload d = pv.wl[wid];
         const uint2 *slab = pv.slab + d.slab;
-        for (int i = 0; i < d.h; ++i) {
-            const uint32_t rid = __ldg(pv.rows + d.rows + i);
-            for (int c0 = 0; c0 < k; c0 += 64) {
-                const int j0 = c0 + 2 * lane;
-                float a0 = 0.f, a1 = 0.f;
-                if (d.w > 0) row_spmm<EVEN>(slab, d, i, X, k, j0, lane, a0, a1);
-                if (rid & kRowSplit) {
-                    const int slot = (int)(rid & 0x7fffffffu);
-                    float *pp = sv.partial + (int64_t)slot * k;
-                    if (j0 < k) pp[j0] = a0;
-                    if (j0 + 1 < k) pp[j0 + 1] = a1;
-                    if (c0 + 64 < k) continue;   // publish after the last column chunk
-                    __threadfence();
-                    __syncwarp();
-                    const int s = sv.slot_owner[slot];
-                    const SplitRow sr = sv.rows[s];
-                    unsigned prev = 0;
-                    if (lane == 0) prev = atomicAdd(sv.counter + s, 1u);
-                    prev = __shfl_sync(kFull, prev, 0);
-                    if (prev != (unsigned)sr.nchunks - 1) continue;
-                    __threadfence();
-                    FSum sr4[4];
-                    for (int cc = 0; cc < k; cc += 64) {
-                        const int jj = cc + 2 * lane;
-                        float t0 = 0.f, t1 = 0.f;
-                        for (int q = 0; q < sr.nchunks; ++q) {
-                            const float *src = sv.partial + (int64_t)(sr.first_slot + q) * k;
-                            if (jj < k) t0 += __ldcg(src + jj);
-                            if (jj + 1 < k) t1 += __ldcg(src + jj + 1);
-                        }
-                        epilogue_k<MODE>(E, sr.row, t0, t1, jj, k, X, Y, seeds, delta_k, sr4);
-                    }
-                    if (lane == 0) sv.counter[s] = 0u;
-                    if (MODE != EPI_RAW && j0 < k) {
-                        double *o = redk + (int64_t)(sv.red_split_base + sr.red_slot) * 2 * k;
-                        o[j0] = sr4[0].value();
-                        o[k + j0] = sr4[2].value();
-                        if (j0 + 1 < k) { o[j0 + 1] = sr4[1].value(); o[k + j0 + 1] = sr4[3].value(); }
-                    }
-                } else {
-                    epilogue_k<MODE>(E, rid, a0, a1, j0, k, X, Y, seeds, delta_k, acc4);
-                }
-            }
-        }
+        const uint32_t *rows = pv.rows + d.rows;
+        if (d.major == 0)
+            spmm_rows<MODE, EVEN>(d, slab, rows, E, sv, X, Y, k, lane, seeds, delta_k, redk, acc4);
+        else
+            spmm_block<MODE, EVEN>(d, slab, rows, E, sv, X, Y, k, lane, seeds, delta_k, redk, acc4,
+                                   spmm_tile + warp * 32 * 32);
     }
     if (MODE != EPI_RAW) {
         // per-block column sums (k <= 64 for the RWR epilogue)
@@ -1129,168 +1233,28 @@ k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__r
     }
 }
 
-// k = 64 specialisation: one row per half-warp (16 lanes x float4 = the 64
-// columns), so a warp keeps two rows and, per lane, four 256-byte X-row
-// gathers in flight.  Entries are fetched 16 at a time (one per lane of the
-// half) and broadcast within the half.  Same layout, split-row handling and
-// per-column sums as k_part_spmm.
-template <int MODE>
-__device__ __forceinline__ void epilogue_k64(float c, int64_t dstart, uint32_t rid, float4 t,
-                                             int j0, const float *__restrict__ X,
-                                             float *__restrict__ Y, const int32_t *seeds,
-                                             const double *delta_k, FSum *acc8)
-{
-    const uint32_t v = rid & kRowIdMask;
-    float4 *yr = reinterpret_cast<float4 *>(Y + (int64_t)v * 64 + j0);
-    if (rid & kRowNotFirst) {
-        const float4 o = *yr;
-        t.x += o.x; t.y += o.y; t.z += o.z; t.w += o.w;
-    }
-    if ((rid & kRowNotLast) || MODE == EPI_RAW) { *yr = t; return; }
-    const float4 xo = *reinterpret_cast<const float4 *>(X + (int64_t)v * 64 + j0);
-    float tt[4] = {t.x, t.y, t.z, t.w}, xx[4] = {xo.x, xo.y, xo.z, xo.w}, f[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int j = j0 + q;
-        const float add = (int)v == __ldg(seeds + j) ? (float)((double)c * delta_k[j] + (1.0 - (double)c)) : 0.f;
-        f[q] = fmaf(c, tt[q], add);
-        acc8[q].add(fabsf(f[q] - xx[q]));
-        if ((int64_t)v >= dstart) acc8[4 + q].add(f[q]);
-    }
-    *yr = make_float4(f[0], f[1], f[2], f[3]);
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(kBlock)
-k_part_spmm64(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__restrict__ Yout,
-              const IterState *__restrict__ st, const int32_t *__restrict__ seeds,
-              const double *__restrict__ delta_k, double *__restrict__ redk)
-{
-    const float *X = Xin;
-    float *Y = Yout;
-    float c = 1.f;
-    int64_t dstart = 0;
-    if (st) {
-        const int par = st->parity;
-        X = st->buf[par];
-        Y = st->buf[par ^ 1];
-        c = (float)st->c;
-        dstart = st->dangling_start;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int half = lane >> 4, hl = lane & 15;
-    const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
-    const int j0 = 4 * hl;
-    const int wid = blockIdx.x * kWarpsPerBlock + warp;
-    FSum acc8[8];
-    if (wid < pv.nwl) {
-        const Workload d = pv.wl[wid];
-        const uint2 *slab = pv.slab + d.slab;
-        for (int i0 = 0; i0 < d.h; i0 += 2) {
-            const int i = i0 + half;
-            const bool has = i < d.h;
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int e0 = 0; e0 < d.w; e0 += 16) {
-                uint2 ent = make_uint2(0xffffffffu, 0u);
-                if (has && e0 + hl < d.w) ent = ld_entry(slab, d, i, e0 + hl);
-                const unsigned vb = __ballot_sync(kFull, (int)ent.x >= 0);
-                const int mine = __popc(vb & hmask);
-                const int tmax = max(mine, __shfl_xor_sync(kFull, mine, 16));
-                for (int t = 0; t < tmax; t += 4) {
-                    float4 xv[4];
-                    float vv[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int cu = __shfl_sync(kFull, (int)ent.x, t + u, 16);
-                        vv[u] = __shfl_sync(kFull, __uint_as_float(ent.y), t + u, 16);
-                        xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (t + u < mine)
-                            xv[u] = __ldg(reinterpret_cast<const float4 *>(X + (int64_t)cu * 64 + j0));
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float w = t + u < mine ? vv[u] : 0.f;
-                        a.x = fmaf(w, xv[u].x, a.x); a.y = fmaf(w, xv[u].y, a.y);
-                        a.z = fmaf(w, xv[u].z, a.z); a.w = fmaf(w, xv[u].w, a.w);
-                    }
-                }
-                if (tmax < 16) break;
-            }
-            if (!has) continue;
-            const uint32_t rid = __ldg(pv.rows + d.rows + i);
-            if (rid & kRowSplit) {
-                const int slot = (int)(rid & 0x7fffffffu);
-                *reinterpret_cast<float4 *>(sv.partial + (int64_t)slot * 64 + j0) = a;
-                __threadfence();
-                __syncwarp(hmask);
-                const int s = sv.slot_owner[slot];
-                const SplitRow sr = sv.rows[s];
-                unsigned prev = 0;
-                if (hl == 0) prev = atomicAdd(sv.counter + s, 1u);
-                prev = __shfl_sync(hmask, prev, 0, 16);
-                if (prev != (unsigned)sr.nchunks - 1) continue;
-                __threadfence();
-                float4 tot = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int q = 0; q < sr.nchunks; ++q) {
-                    const float4 pq = __ldcg(reinterpret_cast<const float4 *>(
-                        sv.partial + (int64_t)(sr.first_slot + q) * 64 + j0));
-                    tot.x += pq.x; tot.y += pq.y; tot.z += pq.z; tot.w += pq.w;
-                }
-                FSum s8[8];
-                epilogue_k64<MODE>(c, dstart, sr.row, tot, j0, X, Y, seeds, delta_k, s8);
-                if (hl == 0) sv.counter[s] = 0u;
-                if (MODE != EPI_RAW) {
-                    double *o = redk + (int64_t)(sv.red_split_base + sr.red_slot) * 128;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) { o[j0 + q] = s8[q].value(); o[64 + j0 + q] = s8[4 + q].value(); }
-                }
-            } else {
-                epilogue_k64<MODE>(c, dstart, rid, a, j0, X, Y, seeds, delta_k, acc8);
-            }
-        }
-    }
-    if (MODE != EPI_RAW) {
-        // both halves hold the same 4 columns: add them, then warps in order
-        __shared__ double sm[kWarpsPerBlock][16][8];
-        double a8[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            a8[q] = acc8[q].value();
-            a8[q] += __shfl_xor_sync(kFull, a8[q], 16);
-        }
-        if (half == 0) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) sm[warp][hl][q] = a8[q];
-        }
-        __syncthreads();
-        if (threadIdx.x < 128) {
-            const int qq = threadIdx.x >> 6, j = threadIdx.x & 63;   // qq 0: L1, 1: dangling
-            double acc = 0.0;
-            for (int w = 0; w < kWarpsPerBlock; ++w) acc += sm[w][j >> 2][qq * 4 + (j & 3)];
-            redk[(int64_t)(pv.red_base + blockIdx.x) * 128 + qq * 64 + j] = acc;
-        }
-    }
-}
-
 void launch_part_spmm(int mode, const PartView &pv, const SplitView &sv, const float *X, float *Y,
                       int k, const IterState *st, const int32_t *seeds, const double *delta_k,
                       double *redk, cudaStream_t s)
 {
     if (pv.nblocks <= 0) return;
     dim3 g(pv.nblocks), b(kBlock);
-    if (k == 64) {
-        if (mode == EPI_RAW) k_part_spmm64<EPI_RAW><<<g, b, 0, s>>>(pv, sv, X, Y, st, seeds, delta_k, redk);
-        else k_part_spmm64<EPI_RWR><<<g, b, 0, s>>>(pv, sv, X, Y, st, seeds, delta_k, redk);
-        count_launches(1);
-        return;
+    const size_t smem = kSpmmTileBytes;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_part_spmm<EPI_RAW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_part_spmm<EPI_RAW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_part_spmm<EPI_RWR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_part_spmm<EPI_RWR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
     }
     const bool even = (k % 2) == 0;
     if (mode == EPI_RAW) {
-        if (even) k_part_spmm<EPI_RAW, true><<<g, b, 0, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
-        else k_part_spmm<EPI_RAW, false><<<g, b, 0, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
+        if (even) k_part_spmm<EPI_RAW, true><<<g, b, smem, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
+        else k_part_spmm<EPI_RAW, false><<<g, b, smem, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
     } else {
-        if (even) k_part_spmm<EPI_RWR, true><<<g, b, 0, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
-        else k_part_spmm<EPI_RWR, false><<<g, b, 0, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
+        if (even) k_part_spmm<EPI_RWR, true><<<g, b, smem, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
+        else k_part_spmm<EPI_RWR, false><<<g, b, smem, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
     }
     count_launches(1);
 }
