@@ -109,6 +109,7 @@ struct spg_format_t {
     DevBuf<float> x, y, stage_in, stage_out;
     DevBuf<double2> red;
     DevBuf<double> redk, delta_k, l1_k;
+    DevBuf<double> colsum;       // first-stage partials of the k-column sums
     DevBuf<float> partial_k;
     DevBuf<int32_t> seeds;
     DevBuf<float> X, Y;
@@ -145,6 +146,7 @@ struct spg_format_t {
         redk.epoch = &epoch;
         delta_k.epoch = &epoch;
         l1_k.epoch = &epoch;
+        colsum.epoch = &epoch;
         seeds.epoch = &epoch;
     }
 
@@ -172,7 +174,7 @@ struct spg_format_t {
         rt_bwd.sched.release();
         redk.release(); delta_k.release(); l1_k.release(); partial_k.release(); seeds.release();
         X.release(); Y.release(); aux.release(); stage_r.release(); init_part.release();
-        z0.release(); z1.release();
+        z0.release(); z1.release(); colsum.release();
         cudaFree(d_state);
         for (auto &kv : graphs) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -1080,7 +1082,8 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
     CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(h->seeds.p, ps.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     launch_onehot_rows(N, k, h->seeds.p, h->X.p, s);
-    launch_init_delta_k(h->d_state, h->X.p, k, h->delta_k.p, s);
+    CK(h->colsum.ensure((size_t)colsum_scratch()));
+    launch_init_delta_k(hs.dangling_start, hs.n, h->X.p, k, h->delta_k.p, h->colsum.p, s);
     SplitView sv = split_of(h, VK);
     sv.partial = h->partial_k.p;
     const std::string key = "rwrk" + std::to_string(k);
@@ -1088,7 +1091,8 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
         for (const PartView &pv : VK.v)
             launch_part_spmm(EPI_RWR, pv, sv, nullptr, nullptr, k, h->d_state, h->seeds.p,
                              h->delta_k.p, h->redk.p, cs);
-        launch_check_k(h->d_state, h->redk.p, nredk, k, h->delta_k.p, h->l1_k.p, cond, uc, cs);
+        launch_check_k(h->d_state, h->redk.p, nredk, k, h->delta_k.p, h->l1_k.p, h->colsum.p, cond,
+                       uc, cs);
     }, &g);
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());

@@ -956,6 +956,8 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
 // lane per column pair.
 
 constexpr int kSpmmU = 8;
+// Blocks of the first stage of the deterministic column sums.
+constexpr int kColsumBlocks = 152;
 constexpr size_t kSpmmTileBytes = (size_t)kWarpsPerBlock * 32 * 32 * sizeof(float2);   // 64 KB
 
 struct EpiK {
@@ -1070,6 +1072,72 @@ __device__ __forceinline__ void spmm_finish(const EpiK &E, const SplitView &sv, 
         epilogue_k<MODE>(E, rid, a0, a1, c0 + 2 * lane, k, X, Y, seeds, delta_k, acc4);
 }
 
+// The operands a row's SpMM epilogue reads besides its sums -- y' (rows
+// continued from an earlier part) and x' (the L1 change) for the lane's two
+// columns -- fetched ahead so that their latency overlaps other rows' work.
+struct RowPreK {
+    float2 yv, xv;
+};
+
+template <int MODE>
+__device__ __forceinline__ RowPreK prefetch_row_k(uint32_t rid, bool ok, const float *__restrict__ X,
+                                                  const float *__restrict__ Y, int k, int j0)
+{
+    RowPreK r{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (!ok || (rid & kRowSplit) || j0 >= k) return r;
+    const int64_t o = (int64_t)(rid & kRowIdMask) * k + j0;
+    const bool two = j0 + 1 < k;
+    if (rid & kRowNotFirst) { r.yv.x = Y[o]; if (two) r.yv.y = Y[o + 1]; }
+    if (MODE != EPI_RAW && !(rid & kRowNotLast)) { r.xv.x = X[o]; if (two) r.xv.y = X[o + 1]; }
+    return r;
+}
+
+// epilogue_k with its row operands prefetched (same arithmetic).
+template <int MODE>
+__device__ __forceinline__ void epilogue_k_pre(const EpiK &E, uint32_t rid, float t0, float t1,
+                                               const RowPreK &r, int j0, int k,
+                                               float *__restrict__ Y, const int32_t *seeds,
+                                               const double *delta_k, FSum *acc4)
+{
+    const uint32_t v = rid & kRowIdMask;
+    float *yr = Y + (int64_t)v * k;
+    const bool h0 = j0 < k, h1 = j0 + 1 < k;
+    if (rid & kRowNotFirst) { t0 += r.yv.x; t1 += r.yv.y; }
+    if ((rid & kRowNotLast) || MODE == EPI_RAW) {
+        if (h0) yr[j0] = t0;
+        if (h1) yr[j0 + 1] = t1;
+        return;
+    }
+    const double c = E.c;
+    if (h0) {
+        float add = (int)v == __ldg(seeds + j0) ? (float)(c * delta_k[j0] + (1.0 - c)) : 0.f;
+        float f = fmaf(E.c, t0, add);
+        yr[j0] = f;
+        acc4[0].add(fabsf(f - r.xv.x));
+        if ((int64_t)v >= E.dstart) acc4[2].add(f);
+    }
+    if (h1) {
+        float add = (int)v == __ldg(seeds + j0 + 1) ? (float)(c * delta_k[j0 + 1] + (1.0 - c)) : 0.f;
+        float f = fmaf(E.c, t1, add);
+        yr[j0 + 1] = f;
+        acc4[1].add(fabsf(f - r.xv.y));
+        if ((int64_t)v >= E.dstart) acc4[3].add(f);
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void spmm_finish_pre(const EpiK &E, const SplitView &sv, uint32_t rid,
+                                                float a0, float a1, const RowPreK &r, int c0, int k,
+                                                int lane, const float *__restrict__ X,
+                                                float *__restrict__ Y, const int32_t *seeds,
+                                                const double *delta_k, double *redk, FSum *acc4)
+{
+    if (rid & kRowSplit)
+        spmm_finish_split<MODE>(E, sv, rid, a0, a1, c0, k, lane, X, Y, seeds, delta_k, redk);
+    else
+        epilogue_k_pre<MODE>(E, rid, a0, a1, r, c0 + 2 * lane, k, Y, seeds, delta_k, acc4);
+}
+
 // Row-major workload: rows one after another, 32 entries per batch.
 template <int MODE, bool EVEN>
 __device__ __forceinline__ void spmm_rows(const Workload &d, const uint2 *__restrict__ slab,
@@ -1084,6 +1152,7 @@ __device__ __forceinline__ void spmm_rows(const Workload &d, const uint2 *__rest
         const int j0 = c0 + 2 * lane;
         for (int i = 0; i < d.h; ++i) {
             const uint32_t rid = __ldg(rows + i);
+            const RowPreK pre = prefetch_row_k<MODE>(rid, true, X, Y, k, j0);
             const uint2 *rs = slab + (int64_t)i * d.w;
             float a0 = 0.f, a1 = 0.f;
             uint2 nxt = d.w > 0 ? __ldcs(rs + lane) : pad;
@@ -1111,7 +1180,7 @@ __device__ __forceinline__ void spmm_rows(const Workload &d, const uint2 *__rest
                 }
                 if (cnt < 32) break;
             }
-            spmm_finish<MODE>(E, sv, rid, a0, a1, c0, k, lane, X, Y, seeds, delta_k, redk, acc4);
+            spmm_finish_pre<MODE>(E, sv, rid, a0, a1, pre, c0, k, lane, X, Y, seeds, delta_k, redk, acc4);
         }
     }
 }
@@ -1166,10 +1235,22 @@ __device__ __forceinline__ void spmm_block(const Workload &d, const uint2 *__res
             __syncwarp();
             const int nr = min(32, d.h - b);
 #pragma unroll 1
-            for (int t = 0; t < nr; ++t) {
-                const uint32_t rid = __shfl_sync(kFull, my_rid, t);
-                const float2 a = tile[t * 32 + lane];
-                spmm_finish<MODE>(E, sv, rid, a.x, a.y, c0, k, lane, X, Y, seeds, delta_k, redk, acc4);
+            for (int t0 = 0; t0 < nr; t0 += 8) {
+                uint32_t rid[8];
+                RowPreK pre[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    rid[u] = __shfl_sync(kFull, my_rid, (t0 + u) & 31);
+                    pre[u] = prefetch_row_k<MODE>(rid[u], t0 + u < nr, X, Y, k, j0);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (t0 + u < nr) {
+                        const float2 a = tile[(t0 + u) * 32 + lane];
+                        spmm_finish_pre<MODE>(E, sv, rid[u], a.x, a.y, pre[u], c0, k, lane, X, Y, seeds,
+                                              delta_k, redk, acc4);
+                    }
+                }
             }
             __syncwarp();
         }
@@ -1319,24 +1400,16 @@ void launch_check(int mode, IterState *st, const double2 *red, int nred,
 
 // Per-column sums over slots for k columns (k <= 64): thread (q, part)
 // sums slots part, part+P, ... of column q in order, then parts in order.
-__global__ void __launch_bounds__(1024)
-k_check_k(IterState *st, const double *__restrict__ redk, int nred, int k, double *delta_k,
+__global__ void __launch_bounds__(128)
+k_check_k(IterState *st, const double *__restrict__ part, int nb, int k, double *delta_k,
           double *l1_k, cudaGraphConditionalHandle cond, int use_cond)
 {
-    __shared__ double part_sum[1024];
     __shared__ double colmax[64];
     if (st->done) return;   // host-loop mode may launch past convergence
     const int Q = 2 * k;
-    const int P = blockDim.x / Q;
-    const int q = threadIdx.x % Q, p = threadIdx.x / Q;
-    double a = 0.0;
-    if (p < P)
-        for (int i = p; i < nred; i += P) a += redk[(int64_t)i * Q + q];
-    part_sum[threadIdx.x] = a;
-    __syncthreads();
     if (threadIdx.x < Q) {
         double t = 0.0;
-        for (int pp = 0; pp < P; ++pp) t += part_sum[pp * Q + threadIdx.x];
+        for (int b = 0; b < nb; ++b) t += part[(int64_t)b * Q + threadIdx.x];
         if (threadIdx.x < k) { l1_k[threadIdx.x] = t; colmax[threadIdx.x] = t; }
         else delta_k[threadIdx.x - k] = t;
     }
@@ -1353,12 +1426,50 @@ k_check_k(IterState *st, const double *__restrict__ redk, int nred, int k, doubl
     }
 }
 
-void launch_check_k(IterState *st, const double *redk, int nred, int k, double *delta_k,
-                    double *l1_k, unsigned long long cond, int use_cond, cudaStream_t s)
+// Deterministic column sums of a row-major block src (rows [row0, row0 +
+// nrows), row stride ld, first Q <= 128 columns), stage 1 of 2: block b sums
+// a fixed contiguous range of rows; thread (p, q) takes every P-th row of it
+// for column q (FP32 sources through a TwoSum pair, FP64 ones in FP64); the P
+// partials are added in order into part[b * Q + q].
+template <class T>
+__global__ void __launch_bounds__(256)
+k_colsum_part(const T *__restrict__ src, int64_t row0, int64_t nrows, int64_t ld, int Q,
+              double *__restrict__ part)
 {
-    k_check_k<<<1, 1024, 0, s>>>(st, redk, nred, k, delta_k, l1_k,
-                                 (cudaGraphConditionalHandle)cond, use_cond);
-    count_launches(1);
+    __shared__ double sm[256];
+    const int P = 256 / Q;
+    const int q = threadIdx.x % Q, p = threadIdx.x / Q;
+    const int64_t per = (nrows + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = row0 + per * blockIdx.x, hi = min(row0 + nrows, lo + per);
+    double a = 0.0;
+    if (p < P) {
+        if (sizeof(T) == sizeof(float)) {
+            FSum f;
+            for (int64_t v = lo + p; v < hi; v += P) f.add((float)src[v * ld + q]);
+            a = f.value();
+        } else {
+            for (int64_t v = lo + p; v < hi; v += P) a += (double)src[v * ld + q];
+        }
+    }
+    sm[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x < Q) {
+        double t = 0.0;
+        for (int pp = 0; pp < P; ++pp) t += sm[pp * Q + threadIdx.x];
+        part[(int64_t)blockIdx.x * Q + threadIdx.x] = t;
+    }
+}
+
+int colsum_scratch() { return kColsumBlocks * 128; }
+
+void launch_check_k(IterState *st, const double *redk, int nred, int k, double *delta_k,
+                    double *l1_k, double *scratch, unsigned long long cond, int use_cond,
+                    cudaStream_t s)
+{
+    k_colsum_part<double><<<kColsumBlocks, 256, 0, s>>>(redk, 0, nred, 2 * k, 2 * k, scratch);
+    k_check_k<<<1, 128, 0, s>>>(st, scratch, kColsumBlocks, k, delta_k, l1_k,
+                                (cudaGraphConditionalHandle)cond, use_cond);
+    count_launches(2);
 }
 
 // Dangling mass of the start vector: a deterministic two-stage sum (fixed
@@ -1423,29 +1534,23 @@ void launch_set_one(float *p, const int32_t *idx, int count, cudaStream_t s)
     count_launches(1);
 }
 
-__global__ void __launch_bounds__(1024)
-k_init_delta_k(const IterState *st, const float *__restrict__ X, int k, double *delta_k)
+__global__ void __launch_bounds__(128)
+k_init_delta_k_final(const double *__restrict__ part, int nb, int k, double *delta_k)
 {
-    __shared__ double part_sum[1024];
-    const int P = blockDim.x / k;
-    const int j = threadIdx.x % k, p = threadIdx.x / k;
-    double a = 0.0;
-    if (p < P)
-        for (int64_t v = st->dangling_start + p; v < st->n; v += P) a += X[v * k + j];
-    part_sum[threadIdx.x] = a;
-    __syncthreads();
     if (threadIdx.x < k) {
         double t = 0.0;
-        for (int pp = 0; pp < P; ++pp) t += part_sum[pp * k + threadIdx.x];
+        for (int b = 0; b < nb; ++b) t += part[(int64_t)b * k + threadIdx.x];
         delta_k[threadIdx.x] = t;
     }
 }
 
-void launch_init_delta_k(const IterState *st, const float *X, int k, double *delta_k,
-                         cudaStream_t s)
+void launch_init_delta_k(int64_t dangling_start, int64_t n, const float *X, int k,
+                         double *delta_k, double *scratch, cudaStream_t s)
 {
-    k_init_delta_k<<<1, 1024, 0, s>>>(st, X, k, delta_k);
-    count_launches(1);
+    const int64_t a = dangling_start;
+    k_colsum_part<float><<<kColsumBlocks, 256, 0, s>>>(X, a, n - a, k, k, scratch);
+    k_init_delta_k_final<<<1, 128, 0, s>>>(scratch, kColsumBlocks, k, delta_k);
+    count_launches(2);
 }
 
 // ------------------------------------------------------- batch of graphs --

@@ -38,7 +38,8 @@ void launch_check(int mode, IterState *st, const double2 *red, int nred,
                   unsigned long long cond, int use_cond, cudaStream_t s);
 // Same for SpMM RWR: per-column l1_k / delta_k, l1 = max over columns.
 void launch_check_k(IterState *st, const double *redk, int nred, int k, double *delta_k,
-                    double *l1_k, unsigned long long cond, int use_cond, cudaStream_t s);
+                    double *l1_k, double *scratch, unsigned long long cond, int use_cond,
+                    cudaStream_t s);
 
 // Dangling mass of buf[parity] (positions >= dangling_start, or the rows
 // flagged in `dangling`) into st->delta; `scratch` holds init_delta_scratch()
@@ -48,8 +49,10 @@ void launch_init_delta_flags(IterState *st, const uint8_t *dangling, double *scr
 int init_delta_scratch();
 // p[idx[i]] = 1 for i < count
 void launch_set_one(float *p, const int32_t *idx, int count, cudaStream_t s);
-void launch_init_delta_k(const IterState *st, const float *X, int k, double *delta_k,
-                         cudaStream_t s);
+void launch_init_delta_k(int64_t dangling_start, int64_t n, const float *X, int k,
+                         double *delta_k, double *scratch, cudaStream_t s);
+// Doubles of scratch the two-stage column sums need (check_k, init_delta_k).
+int colsum_scratch();
 
 // z[i] = p[i] * inv_deg[i] (pattern-only start vectors)
 void launch_scale(int64_t n, const float *p, const float *inv_deg, float *z, cudaStream_t s);
