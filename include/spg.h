@@ -86,9 +86,9 @@ typedef struct {
 /* Build options.  Zero-initialise, then set what you need. */
 typedef struct {
     /* Column tile width (Section 3.1, Solution 1; Algorithm 1).  0 = auto:
-     * the largest power of two whose x slice (tile_width * 4 * vec_width
-     * bytes) fits in 40 % of the L2; < 0 = no dense tiles (the whole matrix is
-     * one composite tile). */
+     * the largest power of two whose x slice (tile_width * 4 bytes) fits in
+     * 40 % of the L2; < 0 = no dense tiles (the whole matrix is one
+     * composite tile). */
     int64_t tile_width;
     /* Workload size per warp (Solution 3).  0 = Algorithm 2. */
     int64_t wl;
@@ -102,7 +102,13 @@ typedef struct {
     /* Maximum resident warps of the whole GPU used by Algorithms 2-3.
      * 0 = query the current device (SMs x resident warps of the kernel). */
     int max_warps;
-    /* Vector width the tiles are sized for: 1 for spmv, k for spmm. */
+    /* Vector width the format is meant for (1 for spmv, k for spmm).  It
+     * does not narrow the auto tiles: on GB300 a k = 64 SpMM ran fastest on
+     * the SpMV tiles (R-MAT scale 22, RWR iteration: 3.57 ms with one part,
+     * 3.69 ms with 1M-column tiles, 4.12 ms with the 128K-column tiles whose
+     * 64-wide x slice fits the L2) -- each extra part re-reads and re-writes
+     * the rows it continues, which costs more than the slice's L2 reuse
+     * saves.  Kept for the ABI; 0 or 1 otherwise. */
     int vec_width;
     /* Also build the transposed layout (for spg_rwr_adjoint). */
     int build_transpose;

@@ -210,8 +210,7 @@ static int64_t resolve_tile_width(const spg_build_opts &o, int64_t l2_bytes)
 {
     if (o.tile_width > 0) return o.tile_width;
     if (o.tile_width < 0) return 0;
-    int vw = o.vec_width > 0 ? o.vec_width : 1;
-    int64_t cols = (int64_t)(0.4 * (double)l2_bytes) / (4 * (int64_t)vw);
+    int64_t cols = (int64_t)(0.4 * (double)l2_bytes) / 4;
     return pow2_floor(std::max<int64_t>(cols, 1024));
 }
 
