@@ -243,3 +243,56 @@ def chung_lu_batch_sizes(count: int, lo_log2: int = 10, hi_log2: int = 17, seed:
     """Node counts log-uniform in [2^lo, 2^hi] for a batch of small graphs."""
     u = _keys_fast(count, seed, 12).astype(np.float64)
     return np.floor(2.0 ** (lo_log2 + u * (hi_log2 - lo_log2))).astype(np.int64)
+
+
+# ------------------------------------------- non-power-law sanity matrices --
+#
+# Matrices with the shapes of the paper's unstructured comparison set (its
+# dense 2K x 2K case and banded / finite-element-like sparsity); values are
+# U[0,1) draws of the counter generator (seeded), so every entry is a
+# positive FP32 and the tolerance bound |M| |x| is simply M x.
+
+def _csr_from_rows(n: int, row_len: np.ndarray, cols: np.ndarray, seed: int):
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(row_len, out=rowptr[1:])
+    val = uniform(int(rowptr[-1]), seed)
+    return rowptr, np.ascontiguousarray(cols, dtype=np.int32), val
+
+
+def dense_matrix(n: int, seed: int = 21):
+    """Every entry of an n x n matrix stored (the paper's dense 2K x 2K case)."""
+    cols = np.tile(np.arange(n, dtype=np.int32), n)
+    return _csr_from_rows(n, np.full(n, n, dtype=np.int64), cols, seed)
+
+
+def banded(n: int, half_width: int, seed: int = 22):
+    """Row i holds columns max(0, i-b) .. min(n-1, i+b)."""
+    i = np.arange(n, dtype=np.int64)
+    lo = np.maximum(0, i - half_width)
+    hi = np.minimum(n - 1, i + half_width)
+    row_len = hi - lo + 1
+    start = np.repeat(lo, row_len)
+    offs = np.arange(int(row_len.sum()), dtype=np.int64) - np.repeat(np.cumsum(row_len) - row_len, row_len)
+    return _csr_from_rows(n, row_len, (start + offs).astype(np.int32), seed)
+
+
+def stencil_3d(nx: int, ny: int, nz: int, seed: int = 23):
+    """27-point stencil of an nx x ny x nz grid (a trilinear finite-element
+    pattern): node (x, y, z) couples to every node within one step along
+    each axis; columns ascending."""
+    n = nx * ny * nz
+    g = np.arange(n, dtype=np.int64)
+    x, y, z = g % nx, (g // nx) % ny, g // (nx * ny)
+    cols = []
+    ok_all = []
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                xx, yy, zz = x + dx, y + dy, z + dz
+                ok = (xx >= 0) & (xx < nx) & (yy >= 0) & (yy < ny) & (zz >= 0) & (zz < nz)
+                cols.append(np.where(ok, xx + nx * (yy + ny * zz), -1))
+                ok_all.append(ok)
+    C = np.stack(cols, axis=1)            # n x 27, ascending within a row
+    K = np.stack(ok_all, axis=1)
+    row_len = K.sum(axis=1).astype(np.int64)
+    return _csr_from_rows(n, row_len, C[K], seed)

@@ -159,6 +159,16 @@ typedef struct {
      * z = p * (1/outdeg) and the epilogue writes both p and z; spmv scales x
      * first.  rwr and spmm need stored values and refuse such handles. */
     int pattern_only;
+    /* Row partition (Section 3.2; PAGERANK handles only): when row_part is
+     * non-NULL (int32[n], part of each node, 0 <= part < nparts, as written
+     * by spg_partition_rows) the handle holds rank part_id's rows of M only
+     * -- the rows v with row_part[v] == part_id -- over all columns, in the
+     * column order of the whole matrix, so that every rank's iterate uses
+     * one permuted order.  Its kernels write only those rows.  The array is
+     * read during the call and not retained.  NULL = all rows. */
+    const int32_t *row_part;
+    int32_t part_id;
+    int32_t nparts;
 } spg_build_opts;
 
 /* Per-call results of the power iterations. */
@@ -269,6 +279,29 @@ spg_status spg_spmm(spg_handle h, const float *X, int64_t ldx, float *Y, int64_t
  * reached. */
 spg_status spg_pagerank(spg_handle h, float damping, double tol, int max_iter,
                         const float *p0, float *p_out, spg_iter_info *info, void *stream);
+
+/* Section 3.2: the bitonic row partition.  Rows of M (nodes, by in-degree
+ * row_len[v], decreasing; ties ascending id) are dealt to P parts in rounds
+ * of P, the dealing direction reversing every round, so that parts get
+ * near-equal rows and entries.  part: int32[n] host output.  P in [1, 64];
+ * SPG_ERR_INVALID otherwise. */
+spg_status spg_partition_rows(int64_t n, const int64_t *row_len, int P, int32_t *part);
+
+/* Row-partitioned PageRank (Section 3.2) over P rank handles, run on the
+ * calling device: ranks[r] must be PAGERANK handles built from the same
+ * graph with the same row_part, nparts = P and part_id = r.  Each
+ * iteration, every rank's tiled-composite kernels produce its own rows of
+ * the next iterate in its own x/y buffers; an all-gather step then gives
+ * every rank the whole vector (on one device: a kernel copying each row
+ * from its owner's buffer into the others', where several GPUs would
+ * all-gather the ranks' row slices and scatter them locally); one check
+ * kernel sums all ranks' (L1 change, dangling mass) partials in a fixed
+ * order -- the all-reduce -- and updates every rank's state.  Same
+ * arguments and result as spg_pagerank (p0 NULL = uniform start); the host
+ * drives the iterations (no graph), P in [1, 8]. */
+spg_status spg_pagerank_ranks(const spg_handle *ranks, int P, float damping, double tol,
+                              int max_iter, const float *p0, float *p_out, spg_iter_info *info,
+                              void *stream);
 
 /* Random Walk with Restart, Appendix F Eq. 9 on M (personalised PageRank):
  * r <- c M r + [v == s] (c * dangling mass + 1 - c), r(0) = e_s, for each of

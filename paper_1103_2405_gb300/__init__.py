@@ -44,7 +44,8 @@ class _Opts(ctypes.Structure):
                 ("keep_csr", ctypes.c_int), ("device", ctypes.c_int), ("split_cost", ctypes.c_double),
                 ("tune_table_path", ctypes.c_char_p), ("x_stage_cols", ctypes.c_int64),
                 ("slab_prefetch", ctypes.c_int64), ("loop_mode", ctypes.c_int),
-                ("max_rows", ctypes.c_int64), ("kernel", ctypes.c_int), ("pattern_only", ctypes.c_int)]
+                ("max_rows", ctypes.c_int64), ("kernel", ctypes.c_int), ("pattern_only", ctypes.c_int),
+                ("row_part", ctypes.c_void_p), ("part_id", ctypes.c_int32), ("nparts", ctypes.c_int32)]
 
 
 class IterInfo(ctypes.Structure):
@@ -75,7 +76,8 @@ EXPORTS = ["spg_build_format", "spg_destroy", "spg_format_info", "spg_tile_info"
            "spg_set_edge_logits", "spg_rwr_weighted", "spg_rwr_adjoint", "spg_build_batch",
            "spg_batch_offsets", "spg_batch_pagerank",
            "spg_baseline_spmv", "spg_baseline_pagerank", "spg_time_parts", "spg_load_table", "spg_launch_count",
-           "spg_status_string", "spg_last_error", "spg_version", "spg_spmv_permuted_noalloc"]
+           "spg_status_string", "spg_last_error", "spg_version", "spg_spmv_permuted_noalloc",
+           "spg_partition_rows", "spg_pagerank_ranks"]
 
 _lib = None
 
@@ -115,6 +117,8 @@ def lib():
             "spg_time_parts": [P, i32, i32, P, P],
             "spg_spmv_permuted_noalloc": [P, P, P, P],
             "spg_load_table": [ctypes.c_char_p],
+            "spg_partition_rows": [i64, P, i32, P],
+            "spg_pagerank_ranks": [P, i32, f32, f64, i32, P, P, ctypes.POINTER(IterInfo), P],
         }
         for name, args in sig.items():
             getattr(L, name).argtypes = args
@@ -198,7 +202,7 @@ class Format:
                  layout_rule=1, max_warps=0, vec_width=1, build_transpose=False, keep_plan=False,
                  keep_csr=False, host_only=False, split_cost=0.0, table=None, x_stage_cols=0,
                  slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, pattern_only=False,
-                 stream=None):
+                 row_part=None, part_id=0, nparts=None, stream=None):
         L = lib()
         self._h = ctypes.c_void_p(None)
         on_dev = _is_torch(rowptr) and rowptr.is_cuda
@@ -220,6 +224,12 @@ class Format:
                      None if tpath is None else str(tpath).encode(), int(x_stage_cols),
                      int(slab_prefetch), int(loop_mode), int(max_rows), int(kernel),
                      int(bool(pattern_only)))
+        if row_part is not None:
+            row_part = np.ascontiguousarray(row_part, dtype=np.int32)
+            opts.row_part = row_part.ctypes.data
+            opts.part_id = int(part_id)
+            opts.nparts = int(nparts) if nparts is not None else (int(row_part.max()) + 1 if row_part.size else 1)
+            self.part_id, self.nparts = int(part_id), int(opts.nparts)
         _check(L.spg_build_format(ctypes.byref(csr), KIND[kind], ctypes.byref(opts),
                                   _stream(stream), ctypes.byref(self._h)))
         self.kind = kind
@@ -412,6 +422,30 @@ def _autograd():
             return dth, None, None, None, None, None
 
     return RWRStationary
+
+
+def partition_rows(row_len, P):
+    """Section 3.2 bitonic row partition (spg_partition_rows): part of each
+    row (int32[n]) for P parts, rows dealt by decreasing length."""
+    rl = np.ascontiguousarray(row_len, dtype=np.int64)
+    part = np.empty(rl.shape[0], np.int32)
+    _check(lib().spg_partition_rows(rl.shape[0], _ptr(rl)[0], int(P), _ptr(part)[0]))
+    return part
+
+
+def pagerank_ranks(ranks, damping=0.85, tol=1e-8, max_iter=1000, p0=None, out=None, like=None,
+                   stream=None):
+    """Row-partitioned PageRank over the rank formats (spg_pagerank_ranks):
+    ranks[r] built with the same row_part and part_id = r."""
+    n = ranks[0].n_graph
+    if out is None:
+        out = _empty_like_vec(like if like is not None else (p0 if p0 is not None else np.empty(0)), n)
+    arr = (ctypes.c_void_p * len(ranks))(*[f._h.value for f in ranks])
+    info = IterInfo()
+    _check(lib().spg_pagerank_ranks(ctypes.cast(arr, ctypes.c_void_p), len(ranks), float(damping),
+                                    float(tol), int(max_iter), _ptr(p0)[0], _ptr(out)[0],
+                                    ctypes.byref(info), _stream(stream)), allow_not_converged=True)
+    return out, info.as_dict()
 
 
 class BatchFormat:

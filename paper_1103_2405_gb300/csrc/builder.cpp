@@ -281,12 +281,13 @@ static int64_t tune_heavy(const std::vector<int32_t> &len, int64_t nnz, const Bu
 bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, std::string &err)
 {
     const int64_t N = src.n;
-    const int64_t nnz = src.colptr[N];
+    const int64_t nnz_src = src.colptr[N];
     const PerfTable &table = perf_table();
     L = Layout();
     L.n = N;
-    L.nnz = nnz;
     L.max_warps = prm.max_warps;
+    // rows this layout holds (all, or one rank's share of a row partition)
+    auto kept = [&](int64_t orig_row) { return !src.row_keep || src.row_keep[orig_row] != 0; };
 
     // 1. column lengths; order by decreasing length, ties ascending id
     std::vector<int64_t> collen((size_t)N);
@@ -330,12 +331,15 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
         parallel_for(N, 1 << 16, [&](int64_t lo, int64_t hi) {
             for (int64_t r = lo; r < hi; ++r) cnt[(size_t)r].store(0, std::memory_order_relaxed);
         });
-        parallel_for(nnz, 1 << 18, [&](int64_t lo, int64_t hi) {
+        parallel_for(nnz_src, 1 << 18, [&](int64_t lo, int64_t hi) {
             for (int64_t k = lo; k < hi; ++k)
-                cnt[(size_t)L.perm[(size_t)src.rowidx[k]]].fetch_add(1, std::memory_order_relaxed);
+                if (kept(src.rowidx[k]))
+                    cnt[(size_t)L.perm[(size_t)src.rowidx[k]]].fetch_add(1, std::memory_order_relaxed);
         });
         for (int64_t r = 0; r < N; ++r) rp[(size_t)r + 1] = rp[(size_t)r] + cnt[(size_t)r].load();
     }
+    const int64_t nnz = rp[(size_t)N];
+    L.nnz = nnz;
     std::vector<int32_t> mcol((size_t)nnz);
     std::vector<float> mval((size_t)nnz);
     std::vector<int64_t> meid;
@@ -349,6 +353,7 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
             for (int64_t j = lo; j < hi; ++j) {
                 int32_t c = L.perm[(size_t)j];
                 for (int64_t k = src.colptr[j]; k < src.colptr[j + 1]; ++k) {
+                    if (!kept(src.rowidx[k])) continue;
                     int64_t r = L.perm[(size_t)src.rowidx[k]];
                     int64_t s = fill[(size_t)r].fetch_add(1, std::memory_order_relaxed);
                     mcol[(size_t)s] = c;
@@ -476,7 +481,7 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
         ph.nwl = (int64_t)wfirst[p].size();
     }
     for (int64_t r = 0; r < N; ++r)
-        if (first_part[(size_t)r] < 0) L.zero_rows.push_back(r);
+        if (first_part[(size_t)r] < 0 && kept(L.inv[(size_t)r])) L.zero_rows.push_back(r);
 
     // 5. packing: offsets
     int64_t nwl_all = 0, nrows_all = 0, nslab = 0, nblocks_all = 0;
@@ -513,7 +518,7 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
     } else {
         L.slab.resize((size_t)nslab);
     }
-    if (prm.track_edges) L.edge_slot.assign((size_t)nnz, -1);
+    if (prm.track_edges) L.edge_slot.assign((size_t)nnz_src, -1);
 
     // split rows (ascending row id per part) and their chunk slots
     std::vector<std::vector<int32_t>> split_first(P);   // per part: row -> first slot (-1)

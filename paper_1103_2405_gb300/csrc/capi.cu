@@ -94,6 +94,12 @@ struct spg_format_t {
     uint8_t *d_dangling = nullptr;
     // HITS: per permuted position, 1 if in the hub half
     uint8_t *d_row_half = nullptr;
+    // row partition (Section 3.2): this handle's rank, the rank count and the
+    // owner rank of every permuted position
+    int32_t part_id = -1, nparts = 0;
+    int8_t *d_owner = nullptr;
+    DevBuf<double2> red_ranks;       // spg_pagerank_ranks: all ranks' reduction slots
+    DevBuf<IterState *> rank_states; // spg_pagerank_ranks: the ranks' states
     // BATCH: graph offsets and per-graph state
     int ngraph = 0;
     std::vector<int64_t> goff;
@@ -165,7 +171,8 @@ struct spg_format_t {
         fwd.free_device();
         if (bwd) bwd->free_device();
         cudaFree(d_rp); cudaFree(d_col); cudaFree(d_val); cudaFree(d_dangling);
-        cudaFree(d_row_half); cudaFree(d_arp); cudaFree(d_acol); cudaFree(d_P);
+        cudaFree(d_row_half); cudaFree(d_arp); cudaFree(d_acol); cudaFree(d_P); cudaFree(d_owner);
+        red_ranks.release(); rank_states.release();
         cudaFree(d_goff); cudaFree(d_gdstart); cudaFree(d_gid); cudaFree(d_giters);
         cudaFree(d_status);
         cudaFree(d_gbase); cudaFree(d_gl1); cudaFree(d_gdelta);
@@ -371,6 +378,19 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
         if (o.pattern_only && kind != SPG_KIND_PAGERANK)
             return fail(SPG_ERR_INVALID, "pattern_only needs a PAGERANK handle");
         prm.pattern_only = o.pattern_only != 0;
+        std::vector<uint8_t> rkeep;
+        if (o.row_part) {
+            if (kind != SPG_KIND_PAGERANK) return fail(SPG_ERR_INVALID, "row_part needs a PAGERANK handle");
+            if (o.nparts < 1 || o.nparts > 64 || o.part_id < 0 || o.part_id >= o.nparts)
+                return fail(SPG_ERR_INVALID, "row_part needs 1 <= nparts <= 64 and 0 <= part_id < nparts");
+            if (o.keep_csr) return fail(SPG_ERR_INVALID, "keep_csr holds the whole matrix: not with row_part");
+            rkeep.resize((size_t)n);
+            for (int64_t v = 0; v < n; ++v) {
+                const int32_t q = o.row_part[v];
+                if (q < 0 || q >= o.nparts) return fail(SPG_ERR_INVALID, "row_part entry out of range");
+                rkeep[(size_t)v] = q == o.part_id ? 1 : 0;
+            }
+        }
         if (o.tune_table_path) {
             std::string err;
             if (!perf_table_load(o.tune_table_path, perf_table(), err)) return fail(SPG_ERR_INVALID, err);
@@ -408,6 +428,7 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
                 }
             });
             src.n = n; src.colptr = rp; src.rowidx = col; src.val = mval.data(); src.eid = nullptr;
+            if (!rkeep.empty()) src.row_keep = rkeep.data();
         } else {  // HITS: B = [[0, A^T], [A, 0]] of Eq. 8
             // column v < n: rows n+u for edges u->v (A's CSC); column n+u: rows v (A's CSR row u)
             std::vector<int64_t> acp, aeid;
@@ -432,11 +453,20 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
         }
         std::string err;
         if (!build_layout(src, prm, h->fwd, err)) return fail(SPG_ERR_INVALID, err);
+        if (o.row_part) {
+            h->part_id = o.part_id;
+            h->nparts = o.nparts;
+        }
 
         if (!h->host_only) {
             st = device_setup(h.get(), o, s);
             if (st != SPG_OK) return st;
             const int64_t N = h->fwd.n;
+            if (o.row_part) {
+                std::vector<int8_t> owner((size_t)N);
+                for (int64_t k = 0; k < N; ++k) owner[(size_t)k] = (int8_t)o.row_part[h->fwd.inv[(size_t)k]];
+                CK(upload(&h->d_owner, owner.data(), owner.size()));
+            }
             if (kind == SPG_KIND_HITS) {
                 std::vector<uint8_t> half((size_t)N);
                 for (int64_t k = 0; k < N; ++k) half[(size_t)k] = h->fwd.inv[(size_t)k] >= n ? 1 : 0;
@@ -1105,6 +1135,109 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
     } else {
         launch_scatter_rows(N, k, L.d_inv, cur, R, k, 1.f, 0.f, s);
     }
+    CK(cudaStreamSynchronize(s));
+    return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
+}
+
+// ---------------------------------------------------- row partition --
+
+extern "C" spg_status spg_partition_rows(int64_t n, const int64_t *row_len, int P, int32_t *part)
+{
+    if (n < 0 || (n > 0 && (!row_len || !part)) || P < 1 || P > 64)
+        return fail(SPG_ERR_INVALID, "partition_rows needs n >= 0, row_len, part and 1 <= P <= 64");
+    // rows by decreasing length, ties ascending id (counting sort)
+    int64_t maxlen = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        if (row_len[v] < 0) return fail(SPG_ERR_INVALID, "negative row length");
+        maxlen = std::max(maxlen, row_len[v]);
+    }
+    std::vector<int64_t> start((size_t)maxlen + 2, 0);
+    for (int64_t v = 0; v < n; ++v) start[(size_t)row_len[v]]++;
+    int64_t run = 0;
+    for (int64_t l = maxlen; l >= 0; --l) { const int64_t c = start[(size_t)l]; start[(size_t)l] = run; run += c; }
+    // the k-th row of the order goes to round k / P, position k % P; odd
+    // rounds deal from the last part back to the first
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t k = start[(size_t)row_len[v]]++;
+        const int64_t round = k / P, pos = k % P;
+        part[v] = (int32_t)((round & 1) ? P - 1 - pos : pos);
+    }
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_pagerank_ranks(const spg_handle *ranks, int P, float damping, double tol,
+                                         int max_iter, const float *p0, float *p_out,
+                                         spg_iter_info *info, void *stream)
+{
+    if (!ranks || P < 1 || P > 8) return fail(SPG_ERR_INVALID, "pagerank_ranks needs 1 <= P <= 8 handles");
+    if (!p_out || !(damping >= 0.f && damping < 1.f) || max_iter < 0)
+        return fail(SPG_ERR_INVALID, "bad pagerank arguments");
+    spg_handle h0 = ranks[0];
+    for (int r = 0; r < P; ++r) {
+        spg_handle h = ranks[r];
+        if (!h || h->host_only || h->kind != SPG_KIND_PAGERANK)
+            return fail(SPG_ERR_INVALID, "every rank needs a device PAGERANK handle");
+        if (h->nparts != P || h->part_id != r || !h->d_owner)
+            return fail(SPG_ERR_INVALID, "rank r must be built with row_part, nparts = P, part_id = r");
+        if (h->fwd.n != h0->fwd.n || h->fwd.perm != h0->fwd.perm || h->fwd.pattern != h0->fwd.pattern)
+            return fail(SPG_ERR_INVALID, "ranks must come from one graph (same order and storage)");
+        if (h->device != h0->device) return fail(SPG_ERR_INVALID, "ranks must share one device");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h0->fwd.n;
+    const bool pat = h0->fwd.pattern;
+    // per rank: its own iterates, state and range of block partials
+    std::vector<int> off((size_t)P + 1, 0);
+    for (int r = 0; r < P; ++r) {
+        spg_handle h = ranks[r];
+        spg_status st = ensure_vectors(h, N);
+        if (st != SPG_OK) return st;
+        if (pat) { CK(h->z0.ensure((size_t)N)); CK(h->z1.ensure((size_t)N)); }
+        off[(size_t)r + 1] = off[(size_t)r] + nred_of(h, get_views(h, true));
+    }
+    CK(h0->red_ranks.ensure((size_t)std::max(1, off[(size_t)P])));
+    CK(h0->rank_states.ensure((size_t)P));
+    std::vector<IterState *> sp((size_t)P);
+    IterState hs{};
+    for (int r = 0; r < P; ++r) {
+        spg_handle h = ranks[r];
+        IterState st = make_state(h, damping, tol, max_iter, N, h->x.p, h->y.p);
+        if (pat) { st.zbuf[0] = h->z0.p; st.zbuf[1] = h->z1.p; st.inv_deg = h->fwd.d_inv_deg; }
+        CK(cudaMemcpyAsync(h->d_state, &st, sizeof st, cudaMemcpyHostToDevice, s));
+        sp[(size_t)r] = h->d_state;
+        if (r == 0) hs = st;
+    }
+    CK(cudaMemcpyAsync(h0->rank_states.p, sp.data(), P * sizeof(IterState *), cudaMemcpyHostToDevice, s));
+    const float *pd = nullptr;
+    if (p0) {
+        spg_status st = device_in(h0, p0, N, &pd, s);
+        if (st != SPG_OK) return st;
+    }
+    for (int r = 0; r < P; ++r) {
+        spg_handle h = ranks[r];
+        if (pd) launch_gather(N, h->fwd.d_inv, pd, h->x.p, s);
+        else launch_fill(N, (float)(1.0 / (double)N), h->x.p, s);
+        if (pat) launch_scale(N, h->x.p, h->fwd.d_inv_deg, h->z0.p, s);
+        CK(h->init_part.ensure((size_t)init_delta_scratch()));
+        launch_init_delta(h->d_state, h->init_part.p, s);
+    }
+    const int nred = off[(size_t)P];
+    LoopGraph lg;   // host-driven iterations: the body is launched once per iteration
+    lg.body = [&](cudaStream_t cs, unsigned long long, int) {
+        for (int r = 0; r < P; ++r)
+            launch_parts(ranks[r], EPI_PAGERANK, nullptr, nullptr, ranks[r]->d_state,
+                         h0->red_ranks.p + off[(size_t)r], cs);
+        launch_allgather_rows(N, h0->d_owner, h0->rank_states.p, P, pat, cs);
+        launch_check_ranks(h0->rank_states.p, P, h0->red_ranks.p, nred, cs);
+    };
+    CK(cudaGetLastError());
+    spg_status st = run_loop(h0, &lg, max_iter, &hs, info, s);
+    if (st != SPG_OK) return st;
+    const bool out_host = !is_device_ptr(p_out);
+    float *od = p_out;
+    if (out_host) { CK(h0->stage_out.ensure((size_t)N)); od = h0->stage_out.p; }
+    launch_scatter_state(N, h0->fwd.d_inv, h0->d_state, od, nullptr, 0, s);
+    if (out_host) CK(cudaMemcpyAsync(p_out, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
 }

@@ -110,6 +110,9 @@ struct ColumnSource {
     const float *val = nullptr;
     const int64_t *eid = nullptr;
     const uint8_t *row_class = nullptr;
+    // rows to hold (by original row id, nullable = all): one rank's share of
+    // a row partition; the column order is still that of the whole matrix
+    const uint8_t *row_keep = nullptr;
 };
 
 // Host builder: order, tile, rank, tune, pack.  Fills `out` (host arrays).

@@ -26,6 +26,14 @@ void count_launches(int64_t k) { g_launches.fetch_add(k); }
 int64_t launch_count() { return g_launches.load(); }
 
 constexpr unsigned kFull = 0xffffffffu;
+// Grid of a grid-stride elementwise kernel: one thread per element up to
+// 64 blocks of 256 per SM.
+static inline int grid_for(int64_t n, int per = 256)
+{
+    int64_t g = (n + per - 1) / per;
+    if (g > 152 * 64) g = 152 * 64;
+    return (int)(g > 0 ? g : 1);
+}
 // Resident blocks per SM the SpMV kernel is compiled for (8 x 8 warps = the
 // SM's 64-warp limit): the gather is latency bound, so occupancy is what
 // keeps enough loads in flight.
@@ -1398,6 +1406,76 @@ void launch_check(int mode, IterState *st, const double2 *red, int nred,
     count_launches(1);
 }
 
+// Row-partitioned PageRank on one device (Section 3.2).  All-gather step:
+// rank r has written the next iterate's rows it owns into its own buffer
+// states[r]->buf[parity ^ 1]; every row is copied from its owner's buffer
+// into the other ranks' (across GPUs: an all-gather of the ranks' row slices
+// and a local scatter).  Pattern-only ranks also carry z = p * inv_deg.
+__global__ void k_allgather_rows(int64_t n, const int8_t *__restrict__ owner,
+                                 IterState *const *states, int P, int pat)
+{
+    __shared__ float *ybuf[8], *zbuf[8];
+    if (threadIdx.x < P) {
+        const IterState *st = states[threadIdx.x];
+        ybuf[threadIdx.x] = st->buf[st->parity ^ 1];
+        zbuf[threadIdx.x] = pat ? st->zbuf[st->parity ^ 1] : nullptr;
+    }
+    __syncthreads();
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int o = owner[v];
+        const float val = ybuf[o][v];
+        const float zv = pat ? zbuf[o][v] : 0.f;
+        for (int q = 0; q < P; ++q) {
+            if (q == o) continue;
+            ybuf[q][v] = val;
+            if (pat) zbuf[q][v] = zv;
+        }
+    }
+}
+
+void launch_allgather_rows(int64_t n, const int8_t *owner, IterState *const *states, int P, bool pat,
+                           cudaStream_t s)
+{
+    k_allgather_rows<<<grid_for(n), 256, 0, s>>>(n, owner, states, P, pat ? 1 : 0);
+    count_launches(1);
+}
+
+// All-reduce step: the ranks' block partials of (L1 change, dangling mass)
+// lie in one buffer; their fixed-order sum goes to every rank's state, which
+// all advance together (the check of k_check, PageRank form).
+__global__ void __launch_bounds__(1024)
+k_check_ranks(IterState *const *states, int P, const double2 *__restrict__ red, int nred)
+{
+    if (states[0]->done) return;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nred; i += blockDim.x) {
+        const double2 v = red[i];
+        a += v.x;
+        b += v.y;
+    }
+    block_sum2_1024(a, b);
+    if (threadIdx.x == 0) {
+        const IterState *s0 = states[0];
+        const int iter = s0->iter + 1;
+        const int done = iter >= s0->max_iter || (s0->tol > 0.0 && a < s0->tol);
+        for (int r = 0; r < P; ++r) {
+            IterState *st = states[r];
+            st->l1 = a;
+            st->delta = b;
+            st->iter = iter;
+            st->parity ^= 1;
+            st->done = done;
+        }
+    }
+}
+
+void launch_check_ranks(IterState *const *states, int P, const double2 *red, int nred, cudaStream_t s)
+{
+    k_check_ranks<<<1, 1024, 0, s>>>(states, P, red, nred);
+    count_launches(1);
+}
+
 // Per-column sums over slots for k columns (k <= 64): thread (q, part)
 // sums slots part, part+P, ... of column q in order, then parts in order.
 __global__ void __launch_bounds__(128)
@@ -1651,12 +1729,6 @@ __global__ void k_batch_init(int64_t n, const IterState *__restrict__ st, float 
 
 // ------------------------------------------------------------- vectors --
 
-static inline int grid_for(int64_t n, int per = 256)
-{
-    int64_t g = (n + per - 1) / per;
-    if (g > 152 * 64) g = 152 * 64;
-    return (int)(g > 0 ? g : 1);
-}
 
 __global__ void k_gather(int64_t n, const int32_t *__restrict__ inv, const float *__restrict__ x,
                          float *__restrict__ xp)

@@ -37,6 +37,11 @@ void launch_part_spmm(int mode, const PartView &pv, const SplitView &sv, const f
 void launch_check(int mode, IterState *st, const double2 *red, int nred,
                   unsigned long long cond, int use_cond, cudaStream_t s);
 // Same for SpMM RWR: per-column l1_k / delta_k, l1 = max over columns.
+// Row-partitioned PageRank on one device: all-gather of the ranks' rows and
+// the all-reduce / check over all ranks' partials.
+void launch_allgather_rows(int64_t n, const int8_t *owner, IterState *const *states, int P, bool pat,
+                           cudaStream_t s);
+void launch_check_ranks(IterState *const *states, int P, const double2 *red, int nred, cudaStream_t s);
 void launch_check_k(IterState *st, const double *redk, int nred, int k, double *delta_k,
                     double *l1_k, double *scratch, unsigned long long cond, int use_cond,
                     cudaStream_t s);

@@ -149,7 +149,7 @@ def test_malformed_csr_rejected(spg, bad):
         col = np.array([1, 2, 0, 0], np.int32)
     csr = spg._Csr(n, nc, nnz, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(col.ctypes.data),
                    None, 0)
-    opts = spg._Opts(0, 0, -1, 1, 64, 1, 0, 0, 0, -1, 0.0, None, 0, 0, 0, 0, 0, 0)
+    opts = spg._Opts(0, 0, -1, 1, 64, 1, 0, 0, 0, -1, 0.0, None, 0, 0, 0, 0, 0, 0, None, 0, 0)
     h = ctypes.c_void_p()
     st = L.spg_build_format(ctypes.byref(csr), 1, ctypes.byref(opts), None, ctypes.byref(h))
     assert st == -1 and not h.value
@@ -190,3 +190,47 @@ def test_bad_table_rejected(spg):
         spg.load_table(path)
     os.unlink(path)
     spg.load_table(None)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 7])
+def test_partition_rows_matches_oracle(spg, P):
+    rp, col = graphgen.rmat(12, 8, seed=2)
+    mrp, _, _ = oracle.build_M(rp, col)
+    rl = np.diff(mrp)
+    part = spg.partition_rows(rl, P)
+    assert np.array_equal(part, oracle.bitonic_partition(rl, P))
+    assert np.array_equal(spg.partition_rows(np.zeros(0, np.int64), P), np.zeros(0, np.int32))
+    with pytest.raises(spg.SpgError):
+        spg.partition_rows(rl, 0)
+
+
+def test_rank_formats_hold_their_rows(spg):
+    # every rank holds exactly its rows of M, over all columns, in the order
+    # of the whole matrix: the union of the ranks' entries is M
+    rp, col = graphgen.rmat(11, 8, seed=3)
+    n = rp.shape[0] - 1
+    mrp, mcol, mval = oracle.build_M(rp, col)
+    P = 3
+    part = spg.partition_rows(np.diff(mrp), P)
+    whole = spg.Format(rp, col, kind="pagerank", host_only=True, max_warps=200)
+    pi, _ = whole.perm()
+    got = []
+    for r in range(P):
+        f = spg.Format(rp, col, kind="pagerank", host_only=True, max_warps=200, row_part=part,
+                       part_id=r, nparts=P)
+        assert np.array_equal(f.perm()[0], pi)
+        rr, cc, vv = f.export_entries()
+        assert np.all(part[rr] == r)
+        assert f.info()["zero_rows"] == int(np.sum((part == r) & (np.diff(mrp) == 0)))
+        got.append((rr, cc, vv))
+    r = np.concatenate([g[0] for g in got]); c = np.concatenate([g[1] for g in got])
+    v = np.concatenate([g[2] for g in got])
+    o = np.lexsort((c, r))
+    mr = np.repeat(np.arange(n), np.diff(mrp))
+    assert np.array_equal(r[o], mr) and np.array_equal(c[o], mcol)
+    assert np.array_equal(v[o].view(np.uint32), mval.view(np.uint32))
+    for bad in (dict(kind="hits"), dict(part_id=3), dict(keep_csr=True)):
+        kw = dict(kind="pagerank", host_only=True, row_part=part, part_id=0, nparts=P)
+        kw.update(bad)
+        with pytest.raises(spg.SpgError):
+            spg.Format(rp, col, **kw)

@@ -75,3 +75,21 @@ def test_seed_picks():
     assert len(set(seeds.tolist())) == 64 and np.all(d[seeds] > 0)
     t = graphgen.pick_targets(rp, col, s, 100, 5)
     assert len(set(t.tolist())) == 100 and graphgen.reachable_from(rp, col, s)[t].all()
+
+
+def test_unstructured_generators_closed_forms():
+    rp, col, val = graphgen.dense_matrix(37)
+    assert rp[-1] == 37 * 37 and np.array_equal(col[:37], np.arange(37))
+    n, b = 1000, 7
+    rp, col, val = graphgen.banded(n, b)
+    assert rp[-1] == n * (2 * b + 1) - b * (b + 1)
+    i = np.repeat(np.arange(n), np.diff(rp))
+    assert np.all(np.abs(col - i) <= b)
+    nx, ny, nz = 5, 4, 3
+    rp, col, val = graphgen.stencil_3d(nx, ny, nz)
+    assert rp[-1] == (3 * nx - 2) * (3 * ny - 2) * (3 * nz - 2)
+    assert np.all(np.diff(rp) <= 27) and np.diff(rp).max() == 27
+    for r in range(nx * ny * nz):
+        seg = col[rp[r]:rp[r + 1]]
+        assert np.all(np.diff(seg) > 0) and r in seg
+    assert val.dtype == np.float32 and np.all((val >= 0) & (val < 1))
