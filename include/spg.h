@@ -151,8 +151,8 @@ typedef struct {
      * 2 = plain 8-warp blocks (no shared memory); 3 = each warp streams its
      * slots into a shared-memory ring with TMA bulk copies (24K x columns
      * staged; measured slower at R-MAT scale 22: 0.33 ms vs 0.23 ms);
-     * 4 = persistent blocks walking each workload as one flat stream of
-     * 32-slot steps, the next batch of loads issued across row ends. */
+     * 4 = persistent 8-warp blocks (six per SM, 48 warps) taking workloads
+     * from a counter, no x slice: more slot loads in flight per SM. */
     int kernel;
     /* PAGERANK handles only: store column indices alone (4 bytes per slot
      * instead of 8).  M = A^T diag(1/outdeg), so the iteration gathers

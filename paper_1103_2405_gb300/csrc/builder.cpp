@@ -732,7 +732,7 @@ std::vector<PartView> Layout::part_views() const
         pv.pf_ahead = 0;
         pv.status = nullptr;
         pv.tma = 0;
-        pv.flat = 0;
+        pv.persist = 0;
         v.push_back(pv);
     }
     return v;

@@ -135,7 +135,8 @@ struct spg_format_t {
     } rt_fwd, rt_bwd;
     int64_t stage_cols = kStagedMaxCols;
     int32_t pf_ahead = 0;        // L2 bulk-prefetch distance of the slot stream (bytes, 0 = off)
-    int kernel = 0;              // 0/1: register stream + staged x slice, 2: plain, 3: TMA ring, 4: flat stream
+    int kernel = 0;              // 0/1: register stream + staged x slice, 2: plain, 3: TMA ring, 4: persistent plain
+    int persist_blocks = 6;      // kernel 4: resident 8-warp blocks per SM
     uint32_t *d_status = nullptr;   // set by kernels whose bounded waits ran out
     int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
     int num_sms = 152;
@@ -316,6 +317,10 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     h->loop_mode = o.loop_mode == 1 ? 1 : 0;
     h->kernel = (o.kernel >= 0 && o.kernel <= 4) ? o.kernel : 0;
     if (o.x_stage_cols < 0 && h->kernel <= 1) h->kernel = 2;   // no shared-memory staging at all
+    if (h->kernel == 4) {
+        const int b = persist_blocks_per_sm();
+        h->persist_blocks = b > 0 ? b : 1;
+    }
     CK(cudaMalloc((void **)&h->d_status, sizeof(uint32_t)));
     CK(cudaMemset(h->d_status, 0, sizeof(uint32_t)));
     CK(h->rt_fwd.sched.ensure(2 * h->fwd.parts.size()));
@@ -679,7 +684,7 @@ extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, in
 static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
                                         spg_format_t::LayoutRT &rt, bool staged)
 {
-    staged = staged && (h->stage_cols > 0 || h->kernel == 3) && h->kernel != 2 && rt.sched.p;
+    staged = staged && (h->stage_cols > 0 || h->kernel >= 3) && h->kernel != 2 && rt.sched.p;
     spg_format_t::Views &V = staged ? rt.vstaged : rt.vplain;
     if (V.built) return V;
     int32_t base = 0;
@@ -698,7 +703,13 @@ static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
         pv.pf_ahead = h->pf_ahead;
         pv.status = h->d_status;
         const int64_t width = ph.c1 - ph.c0;
-        if (staged && h->kernel == 3 && !L.pattern && ph.nwl_total > 0) {
+        if (staged && h->kernel == 4 && ph.nwl_total > 0) {
+            // persistent 8-warp blocks, kPersistBlocksPerSM per SM, no x slice
+            pv.persist = 1;
+            pv.xs_cols = 0;
+            pv.nblocks = (int32_t)std::min<int64_t>((int64_t)h->num_sms * h->persist_blocks,
+                                                    (ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        } else if (staged && h->kernel == 3 && !L.pattern && ph.nwl_total > 0) {
             // TMA-pipelined persistent kernel (x slice when the part is wide enough)
             pv.tma = 1;
             pv.xs_cols = width >= 1024 ? (int32_t)std::min<int64_t>(kTmaMaxCols, width) : 0;
@@ -706,7 +717,6 @@ static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
         } else if (staged && width >= 1024 && ph.nwl_total > 0) {
             pv.xs_cols = (int32_t)std::min<int64_t>(h->stage_cols, width);
             pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
-            pv.flat = h->kernel == 4 ? 1 : 0;
         } else {
             pv.xs_cols = 0;
             pv.nblocks = (int32_t)((ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);

@@ -44,12 +44,13 @@ constexpr int kPartMinBlocks = SPG_PART_MINB;
 // Staged variant: one 32-warp block per SM sharing up to kStagedMaxCols
 // floats (192 KB) of x in shared memory.
 constexpr int kStagedBlock = 1024;
-// Flat-stream variant: fewer warps with more registers each (B slots and B
-// gathers in flight per lane).
-#ifndef SPG_FLAT_BLOCK
-#define SPG_FLAT_BLOCK 768
+// Persistent plain variant: 8-warp blocks, kPersistMinBlocks per SM, no x
+// slice -- more resident warps (more slot loads in flight) than the staged
+// kernel's one 32-warp block.
+#ifndef SPG_PERSIST_MINB
+#define SPG_PERSIST_MINB 6
 #endif
-constexpr int kFlatBlock = SPG_FLAT_BLOCK;
+constexpr int kPersistMinBlocks = SPG_PERSIST_MINB;
 
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -494,88 +495,6 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
     }
 }
 
-// Flat-stream variant of do_workload (kernel option 4).  The warp walks
-// its workload as one sequence of 32-slot steps -- row after row for a
-// row-major workload, column after column of each 32-row block for a
-// column-major one -- in batches of B steps: the gathers of a batch are
-// issued, then the loads of the next batch, then the batch is summed.  The
-// slot loads therefore stay in flight across row boundaries (no drain at the
-// end of every row) and every lane keeps B slots and B gathers outstanding.
-// Row-major rows end on step boundaries (w is a multiple of 32); the
-// warp-uniform test `t + u + 1 == rend` finishes a row inside a batch.
-template <int MODE, class G>
-__device__ __forceinline__ void do_workload_flat(const Workload &d, const PartView &pv,
-                                                 const SplitView &sv, const G &g, const Epi &E,
-                                                 const float *__restrict__ x, float *__restrict__ y,
-                                                 double2 *red, int lane, FSum &r0, FSum &r1)
-{
-    constexpr int B = is_pattern(MODE) ? 16 : 8;
-    const uint2 pad = make_uint2(0xffffffffu, 0u);
-    const uint32_t *__restrict__ rows = pv.rows + d.rows;
-    const Slots<is_pattern(MODE)> slab{pv, d.slab};
-    if (d.major == 0) {
-        const int nst = d.w >> 5;
-        const int T = d.h * nst;
-        uint2 a[B];
-#pragma unroll
-        for (int u = 0; u < B; ++u) a[u] = u < T ? slab.ld((int64_t)u * 32 + lane) : pad;
-        RowPre mine = prefetch_row<MODE>(E, rows, lane, lane < d.h, x, y);
-        int r = 0, rend = nst;
-        float acc = 0.f;
-        for (int t = 0; t < T; t += B) {
-            float xv[B], vv[B];
-#pragma unroll
-            for (int u = 0; u < B; ++u) {
-                const int c = (int)a[u].x;
-                xv[u] = c >= 0 ? g(c) : 0.f;
-                vv[u] = __uint_as_float(a[u].y);
-            }
-#pragma unroll
-            for (int u = 0; u < B; ++u)
-                a[u] = t + B + u < T ? slab.ld((int64_t)(t + B + u) * 32 + lane) : pad;
-#pragma unroll
-            for (int u = 0; u < B; ++u) {
-                acc = fmaf(vv[u], xv[u], acc);
-                if (t + u + 1 == rend) {
-                    const float tot = warp_sum(acc);
-                    const RowPre p = shfl_row(mine, r & 31);
-                    if (lane == 0) finish_row_pre<MODE>(E, sv, red, p, tot, x, y, r0, r1);
-                    acc = 0.f;
-                    ++r;
-                    rend = r < d.h ? rend + nst : INT_MAX;
-                    if ((r & 31) == 0 && r < d.h)
-                        mine = prefetch_row<MODE>(E, rows, r + lane, r + lane < d.h, x, y);
-                }
-            }
-        }
-    } else {
-        const int hp = (d.h + 31) & ~31;
-        for (int b = 0; b < hp; b += 32) {
-            const RowPre p = prefetch_row<MODE>(E, rows, b + lane, b + lane < d.h, x, y);
-            const int64_t s0 = (int64_t)b * d.w + lane;
-            uint2 a[B];
-#pragma unroll
-            for (int u = 0; u < B; ++u) a[u] = u < d.w ? slab.ld(s0 + (int64_t)u * 32) : pad;
-            float acc = 0.f;
-            for (int e = 0; e < d.w; e += B) {
-                float xv[B], vv[B];
-#pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    const int c = (int)a[u].x;
-                    xv[u] = c >= 0 ? g(c) : 0.f;
-                    vv[u] = __uint_as_float(a[u].y);
-                }
-#pragma unroll
-                for (int u = 0; u < B; ++u)
-                    a[u] = e + B + u < d.w ? slab.ld(s0 + (int64_t)(e + B + u) * 32) : pad;
-#pragma unroll
-                for (int u = 0; u < B; ++u) acc = fmaf(vv[u], xv[u], acc);
-            }
-            if (b + lane < d.h) finish_row_pre<MODE>(E, sv, red, p, acc, x, y, r0, r1);
-        }
-    }
-}
-
 template <int MODE>
 __device__ __forceinline__ void resolve_xy(const IterState *st, const float *&x, float *&y)
 {
@@ -616,8 +535,8 @@ k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restri
 // Section 3.1 Solution 1), then its warps take workloads in order from a
 // counter (pv.sched[0]); the last warp out resets the counters for the next
 // launch (pv.sched[1] counts finished warps).  No waits between blocks.
-template <int MODE, bool FLAT>
-__global__ void __launch_bounds__(FLAT ? kFlatBlock : kStagedBlock, 1)
+template <int MODE, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
 k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
               float *__restrict__ yout, const IterState *__restrict__ st,
               double2 *__restrict__ red)
@@ -646,8 +565,7 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
         if (lane == 0) w = atomicAdd(pv.sched, 1u);
         w = __shfl_sync(kFull, w, 0);
         if (w >= (unsigned)pv.nwl) break;
-        if (FLAT) do_workload_flat<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, r0, r1);
-        else do_workload<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, r0, r1);
+        do_workload<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, r0, r1);
     }
     if (lane == 0) {
         const unsigned done = atomicAdd(pv.sched + 1, 1u);
@@ -874,6 +792,15 @@ template <int MODE> static void launch_tma(const PartView &pv, const SplitView &
         pv, sv, x, y, st, red);
 }
 
+int persist_blocks_per_sm()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_part_staged<EPI_PAGERANK, kBlock, kPersistMinBlocks>,
+                                                      kBlock, 0) != cudaSuccess)
+        return 0;
+    return b;
+}
+
 int part_blocks_per_sm()
 {
     int b = 0;
@@ -888,17 +815,15 @@ template <int MODE> static void launch_staged(const PartView &pv, const SplitVie
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_part_staged<MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kStagedMaxCols * (int)sizeof(float));
-        cudaFuncSetAttribute(k_part_staged<MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_part_staged<MODE, kStagedBlock, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kStagedMaxCols * (int)sizeof(float));
         attr = true;
     }
-    const size_t smem = (size_t)pv.xs_cols * sizeof(float);
-    if (pv.flat)
-        k_part_staged<MODE, true><<<pv.nblocks, kFlatBlock, smem, s>>>(pv, sv, x, y, st, red);
+    if (pv.persist)
+        k_part_staged<MODE, kBlock, kPersistMinBlocks><<<pv.nblocks, kBlock, 0, s>>>(pv, sv, x, y, st, red);
     else
-        k_part_staged<MODE, false><<<pv.nblocks, kStagedBlock, smem, s>>>(pv, sv, x, y, st, red);
+        k_part_staged<MODE, kStagedBlock, 1><<<pv.nblocks, kStagedBlock, (size_t)pv.xs_cols * sizeof(float), s>>>(
+            pv, sv, x, y, st, red);
 }
 
 void launch_part(int mode, const PartView &pv, const SplitView &sv, const float *x, float *y,
@@ -917,7 +842,7 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
         count_launches(1);
         return;
     }
-    if (pv.xs_cols > 0) {
+    if (pv.xs_cols > 0 || pv.persist) {
         switch (mode) {
         case EPI_RAW: launch_staged<EPI_RAW>(pv, sv, x, y, st, red, s); break;
         case EPI_PAGERANK: launch_staged<EPI_PAGERANK>(pv, sv, x, y, st, red, s); break;

@@ -101,6 +101,8 @@ void launch_edge_grad(int64_t n, const int64_t *a_rp, const int32_t *a_col, cons
                       cudaStream_t s);
 
 // Resident blocks per SM of the tiled-composite SpMV kernel on this device.
+// Resident blocks per SM of the persistent plain SpMV kernel (kernel option 4).
+int persist_blocks_per_sm();
 int part_blocks_per_sm();
 
 // Batch of graphs: per-graph L1 change and dangling mass (one block per

@@ -63,7 +63,7 @@ struct PartView {
     int32_t xs_cols;      // > 0: columns [c0, c0 + xs_cols) staged in shared memory
     int32_t pf_ahead;     // bytes of a workload's slots prefetched into L2 ahead of use (0 = off)
     int32_t tma;          // 1: slots streamed into shared memory by TMA bulk copies
-    int32_t flat;         // 1: persistent kernel walks workloads as flat step streams
+    int32_t persist;      // 1: persistent 8-warp blocks without an x slice
 };
 
 // TMA-pipelined kernel: per warp a ring of kTmaStages chunks of kTmaChunk

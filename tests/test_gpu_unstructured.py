@@ -25,10 +25,12 @@ def _mat(kind):
 
 
 @pytest.mark.parametrize("kind", ["dense2k", "banded", "stencil"])
-@pytest.mark.parametrize("opts", [dict(), dict(kernel=2), dict(tile_width=1024)])
+@pytest.mark.parametrize("opts", [dict(), dict(kernel=2), dict(tile_width="n/8")])
 def test_unstructured_spmv(kind, opts):
     rp, col, val = _mat(kind)
     n = rp.shape[0] - 1
+    if opts.get("tile_width") == "n/8":   # several dense tiles (at most 126 parts)
+        opts = dict(tile_width=max(256, 1 << int(np.log2(n / 8))))
     f = spg.Format(rp, col, val, kind="matrix", **opts)
     x = graphgen.uniform(n, 2)
     y = f.spmv(torch.from_numpy(x).to(DEV))
