@@ -151,7 +151,7 @@ typedef struct {
      * 2 = plain 8-warp blocks (no shared memory); 3 = each warp streams its
      * slots into a shared-memory ring with TMA bulk copies (24K x columns
      * staged; measured slower at R-MAT scale 22: 0.33 ms vs 0.23 ms);
-     * 4 = persistent 8-warp blocks (six per SM, 48 warps) taking workloads
+     * 4 = persistent 8-warp blocks (five per SM, 40 warps) taking workloads
      * from a counter, no x slice: more slot loads in flight per SM. */
     int kernel;
     /* PAGERANK handles only: store column indices alone (4 bytes per slot
@@ -169,6 +169,12 @@ typedef struct {
     const int32_t *row_part;
     int32_t part_id;
     int32_t nparts;
+    /* Persistent SpMV kernels (options 0, 1, 4): consecutive workloads a warp
+     * takes per claim on the work counter, 1..64; 0 = auto (about 16 claims
+     * per resident warp per part).  One atomic on one address per claim
+     * bounds the claim rate, so parts of many small workloads claim several
+     * at a time. */
+    int32_t claim;
 } spg_build_opts;
 
 /* Per-call results of the power iterations. */

@@ -733,6 +733,8 @@ std::vector<PartView> Layout::part_views() const
         pv.status = nullptr;
         pv.tma = 0;
         pv.persist = 0;
+        pv.claim = 1;
+        pv.pad_ = 0;
         v.push_back(pv);
     }
     return v;

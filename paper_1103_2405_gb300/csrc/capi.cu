@@ -136,7 +136,8 @@ struct spg_format_t {
     int64_t stage_cols = kStagedMaxCols;
     int32_t pf_ahead = 0;        // L2 bulk-prefetch distance of the slot stream (bytes, 0 = off)
     int kernel = 0;              // 0/1: register stream + staged x slice, 2: plain, 3: TMA ring, 4: persistent plain
-    int persist_blocks = 6;      // kernel 4: resident 8-warp blocks per SM
+    int persist_blocks = 5;      // kernel 4: resident 8-warp blocks per SM
+    int claim = 0;               // workloads per scheduler claim (0 = auto)
     uint32_t *d_status = nullptr;   // set by kernels whose bounded waits ran out
     int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
     int num_sms = 152;
@@ -317,6 +318,7 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     h->loop_mode = o.loop_mode == 1 ? 1 : 0;
     h->kernel = (o.kernel >= 0 && o.kernel <= 4) ? o.kernel : 0;
     if (o.x_stage_cols < 0 && h->kernel <= 1) h->kernel = 2;   // no shared-memory staging at all
+    h->claim = (int)std::max<int64_t>(0, std::min<int64_t>(o.claim, 64));
     if (h->kernel == 4) {
         const int b = persist_blocks_per_sm();
         h->persist_blocks = b > 0 ? b : 1;
@@ -681,6 +683,10 @@ extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, in
 // shared memory, one block per SM; the rest (and every part when staging is
 // off) get 8-warp blocks, one warp per workload.  Block reduction slots are
 // laid out part after part; split rows reduce after all blocks.
+// Auto claim size: a part's workloads spread over about this many claims
+// per resident warp.
+constexpr int64_t kClaimsPerWarp = 16;
+
 static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
                                         spg_format_t::LayoutRT &rt, bool staged)
 {
@@ -720,6 +726,14 @@ static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
         } else {
             pv.xs_cols = 0;
             pv.nblocks = (int32_t)((ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        }
+        // claim size: about kClaimsPerWarp claims per resident warp over the part
+        if (pv.persist || pv.xs_cols > 0) {
+            const int64_t warps = (int64_t)pv.nblocks * (pv.persist ? kWarpsPerBlock : 32);
+            const int64_t g = h->claim > 0 ? h->claim : (ph.nwl_total + warps * kClaimsPerWarp - 1) / (warps * kClaimsPerWarp);
+            pv.claim = (int32_t)std::max<int64_t>(1, std::min<int64_t>(g, 64));
+        } else {
+            pv.claim = 1;
         }
         pv.red_base = base;
         base += pv.nblocks;
