@@ -169,12 +169,13 @@ typedef struct {
     const int32_t *row_part;
     int32_t part_id;
     int32_t nparts;
-    /* Persistent SpMV kernels (options 0, 1, 4): consecutive workloads a warp
-     * takes per claim on the work counter, 1..64; 0 = auto (about 16 claims
-     * per resident warp per part).  One atomic on one address per claim
-     * bounds the claim rate, so parts of many small workloads claim several
-     * at a time. */
-    int32_t claim;
+    /* Persistent SpMV kernels (options 0, 1, 4): warps take work from a
+     * counter in claim units, runs of consecutive workloads grouped until
+     * their cost (padded slots + 4 per row) reaches unit_slots; a workload
+     * at least that large is a unit alone.  One atomic on one address per
+     * claim bounds the claim rate, which small workloads would otherwise
+     * hit.  0 = auto (2048), 1 = one workload per claim. */
+    int64_t unit_slots;
 } spg_build_opts;
 
 /* Per-call results of the power iterations. */

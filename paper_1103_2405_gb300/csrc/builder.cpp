@@ -506,6 +506,31 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
         nblocks_all += ph.nblocks;
     }
     if (nwl_all > INT32_MAX || nrows_all > INT32_MAX) { err = "layout too large"; return false; }
+    // claim units: runs of consecutive workloads of one part whose cost
+    // (padded slots + 4 per row) reaches unit_slots, so that a warp's one
+    // claim on the work counter covers several small workloads while a
+    // large one stays alone
+    L.units.clear();
+    for (int64_t p = 0; p < P; ++p) {
+        PartHost &ph = L.parts[(size_t)p];
+        ph.unit_off = (int64_t)L.units.size();
+        const int64_t zr = (int64_t)L.zero_rows.size();
+        int64_t acc = 0;
+        for (int64_t j = 0; j < ph.nwl_total; ++j) {
+            int64_t cost;
+            if (j < ph.nwl) {
+                const int64_t w = ww[p][(size_t)j], h = wh[p][(size_t)j];
+                cost = (wm[p][(size_t)j] == 0 ? h * ru32(w) : ru32(h) * w) + 4 * h;
+            } else {
+                cost = 4 * std::min<int64_t>(kZeroRowsPerWorkload, zr - (j - ph.nwl) * kZeroRowsPerWorkload);
+            }
+            if (acc == 0) L.units.push_back((int32_t)j);
+            acc += cost;
+            if (prm.unit_slots <= 1 || acc >= prm.unit_slots) acc = 0;
+        }
+        ph.nunits = (int64_t)L.units.size() - ph.unit_off;
+        L.units.push_back((int32_t)ph.nwl_total);
+    }
     L.padded_slots = nslab;
     L.wl.resize((size_t)nwl_all);
     L.rows.resize((size_t)nrows_all);
@@ -678,6 +703,7 @@ cudaError_t upload_layout(Layout &L, bool keep_host, cudaStream_t s)
     SPG_UP(d_perm, perm);
     SPG_UP(d_inv, inv);
     SPG_UP(d_wl, wl);
+    SPG_UP(d_units, units);
     SPG_UP(d_rows, rows);
     if (L.pattern) { SPG_UP(d_slab4, slab4); SPG_UP(d_inv_deg, inv_deg); }
     else SPG_UP(d_slab, slab);
@@ -695,6 +721,7 @@ cudaError_t upload_layout(Layout &L, bool keep_host, cudaStream_t s)
     L.on_device = true;
     if (!keep_host) {
         std::vector<Workload>().swap(L.wl);
+        std::vector<int32_t>().swap(L.units);
         std::vector<uint32_t>().swap(L.rows);
         std::vector<uint2>().swap(L.slab);
         std::vector<uint32_t>().swap(L.slab4);
@@ -704,11 +731,11 @@ cudaError_t upload_layout(Layout &L, bool keep_host, cudaStream_t s)
 
 void Layout::free_device()
 {
-    cudaFree(d_perm); cudaFree(d_inv); cudaFree(d_wl); cudaFree(d_rows); cudaFree(d_slab);
+    cudaFree(d_perm); cudaFree(d_inv); cudaFree(d_wl); cudaFree(d_units); cudaFree(d_rows); cudaFree(d_slab);
     cudaFree(d_split); cudaFree(d_slot_owner); cudaFree(d_partial); cudaFree(d_counter);
     cudaFree(d_edge_slot); cudaFree(d_slab4); cudaFree(d_inv_deg);
     d_slab4 = nullptr; d_inv_deg = nullptr;
-    d_perm = d_inv = nullptr; d_wl = nullptr; d_rows = nullptr; d_slab = nullptr;
+    d_perm = d_inv = nullptr; d_wl = nullptr; d_units = nullptr; d_rows = nullptr; d_slab = nullptr;
     d_split = nullptr; d_slot_owner = nullptr; d_partial = nullptr; d_counter = nullptr;
     d_edge_slot = nullptr;
     on_device = false;
@@ -733,8 +760,8 @@ std::vector<PartView> Layout::part_views() const
         pv.status = nullptr;
         pv.tma = 0;
         pv.persist = 0;
-        pv.claim = 1;
-        pv.pad_ = 0;
+        pv.units = d_units + ph.unit_off;
+        pv.nunits = (int32_t)ph.nunits;
         v.push_back(pv);
     }
     return v;

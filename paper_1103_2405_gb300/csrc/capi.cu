@@ -25,6 +25,7 @@
 using namespace spg;
 
 // Default cap on the rows of one workload (spg_build_opts.max_rows = 0).
+static constexpr int64_t kDefaultUnitSlots = 2048;   // claim unit cost (measured)
 static constexpr int64_t kDefaultMaxRows = 32;
 
 static thread_local std::string g_err;
@@ -137,7 +138,6 @@ struct spg_format_t {
     int32_t pf_ahead = 0;        // L2 bulk-prefetch distance of the slot stream (bytes, 0 = off)
     int kernel = 0;              // 0/1: register stream + staged x slice, 2: plain, 3: TMA ring, 4: persistent plain
     int persist_blocks = 5;      // kernel 4: resident 8-warp blocks per SM
-    int claim = 0;               // workloads per scheduler claim (0 = auto)
     uint32_t *d_status = nullptr;   // set by kernels whose bounded waits ran out
     int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
     int num_sms = 152;
@@ -318,7 +318,6 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     h->loop_mode = o.loop_mode == 1 ? 1 : 0;
     h->kernel = (o.kernel >= 0 && o.kernel <= 4) ? o.kernel : 0;
     if (o.x_stage_cols < 0 && h->kernel <= 1) h->kernel = 2;   // no shared-memory staging at all
-    h->claim = (int)std::max<int64_t>(0, std::min<int64_t>(o.claim, 64));
     if (h->kernel == 4) {
         const int b = persist_blocks_per_sm();
         h->persist_blocks = b > 0 ? b : 1;
@@ -385,6 +384,7 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
         if (o.pattern_only && kind != SPG_KIND_PAGERANK)
             return fail(SPG_ERR_INVALID, "pattern_only needs a PAGERANK handle");
         prm.pattern_only = o.pattern_only != 0;
+        prm.unit_slots = o.unit_slots > 0 ? o.unit_slots : kDefaultUnitSlots;
         std::vector<uint8_t> rkeep;
         if (o.row_part) {
             if (kind != SPG_KIND_PAGERANK) return fail(SPG_ERR_INVALID, "row_part needs a PAGERANK handle");
@@ -683,10 +683,6 @@ extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, in
 // shared memory, one block per SM; the rest (and every part when staging is
 // off) get 8-warp blocks, one warp per workload.  Block reduction slots are
 // laid out part after part; split rows reduce after all blocks.
-// Auto claim size: a part's workloads spread over about this many claims
-// per resident warp.
-constexpr int64_t kClaimsPerWarp = 16;
-
 static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
                                         spg_format_t::LayoutRT &rt, bool staged)
 {
@@ -727,14 +723,8 @@ static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
             pv.xs_cols = 0;
             pv.nblocks = (int32_t)((ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
         }
-        // claim size: about kClaimsPerWarp claims per resident warp over the part
-        if (pv.persist || pv.xs_cols > 0) {
-            const int64_t warps = (int64_t)pv.nblocks * (pv.persist ? kWarpsPerBlock : 32);
-            const int64_t g = h->claim > 0 ? h->claim : (ph.nwl_total + warps * kClaimsPerWarp - 1) / (warps * kClaimsPerWarp);
-            pv.claim = (int32_t)std::max<int64_t>(1, std::min<int64_t>(g, 64));
-        } else {
-            pv.claim = 1;
-        }
+        pv.units = L.d_units + ph.unit_off;
+        pv.nunits = (int32_t)ph.nunits;
         pv.red_base = base;
         base += pv.nblocks;
         V.v.push_back(pv);
@@ -1430,6 +1420,8 @@ extern "C" spg_status spg_spmv_permuted_noalloc(spg_handle h, const float *x_per
         pv.rows = L.d_rows;
         pv.slab = L.d_slab;
         pv.slab4 = L.d_slab4;
+        pv.units = L.d_units + ph.unit_off;
+        pv.nunits = (int32_t)ph.nunits;
         pv.sched = sched + 2 * p;
         pv.nwl = (int32_t)ph.nwl_total;
         pv.c0 = (int32_t)ph.c0;
@@ -1598,6 +1590,7 @@ extern "C" spg_status spg_build_batch(const spg_csr *graphs, int count,
         prm.layout_rule = o.layout_rule == 0 ? 0 : 1;
         prm.max_warps = o.max_warps > 0 ? o.max_warps : (h->host_only ? 9728 : query_max_warps());
         prm.max_rows = o.max_rows < 0 ? 0 : (o.max_rows > 0 ? o.max_rows : kDefaultMaxRows);
+        prm.unit_slots = o.unit_slots > 0 ? o.unit_slots : kDefaultUnitSlots;
         if (o.split_cost > 0) prm.split_cost = o.split_cost;
         prm.keep_plan = o.keep_plan != 0;
         prm.seg_off = h->goff.data();

@@ -42,6 +42,10 @@ struct BuildParams {
     // [seg_off[g], seg_off[g+1]); the degree order is taken within each segment
     const int64_t *seg_off = nullptr;
     int64_t nseg = 0;
+    // claim units of the persistent kernels: consecutive workloads grouped
+    // until their cost (padded slots + 4 per row) reaches this; <= 1 = one
+    // workload per unit
+    int64_t unit_slots = 0;
 };
 
 struct PartHost {
@@ -49,6 +53,7 @@ struct PartHost {
     int64_t heavy = 0, wl = 0, nnz = 0, nvirt = 0;
     int64_t nwl = 0;          // regular workloads
     int64_t nwl_total = 0;    // + zero-row workloads
+    int64_t unit_off = 0, nunits = 0;   // claim units: units[unit_off .. unit_off + nunits] (+ end)
     int64_t wl_off = 0;       // first workload in the concatenated array
     int32_t nblocks = 0, red_base = 0;
     double predicted_s = 0;
@@ -71,6 +76,7 @@ struct Layout {
     std::vector<int64_t> zero_rows;
     // packed arrays (host copy; released after upload unless kept)
     std::vector<Workload> wl;
+    std::vector<int32_t> units;         // per part: first workload of each claim unit, then the end
     std::vector<uint32_t> rows;
     std::vector<uint2> slab;
     std::vector<uint32_t> slab4;        // pattern-only slots
@@ -82,6 +88,7 @@ struct Layout {
     // device copies
     int32_t *d_perm = nullptr, *d_inv = nullptr;
     Workload *d_wl = nullptr;
+    int32_t *d_units = nullptr;
     uint32_t *d_rows = nullptr;
     uint2 *d_slab = nullptr;
     uint32_t *d_slab4 = nullptr;

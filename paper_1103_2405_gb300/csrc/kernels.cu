@@ -533,10 +533,11 @@ k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restri
 // memory: one persistent 32-warp block per SM copies x[c0, c0 + S) into
 // shared memory (the GB300 counterpart of the paper's texture-cache tile,
 // Section 3.1 Solution 1), then its warps take workloads in order from a
-// counter (pv.sched[0]), pv.claim consecutive ones per claim (one atomic on
-// one address per claim bounds the claim rate when workloads are small);
-// the last warp out resets the counters for the next launch (pv.sched[1]
-// counts finished warps).  No waits between blocks.
+// counter (pv.sched[0]) in claim units -- runs of consecutive workloads
+// grouped by the builder so that small workloads are claimed several at a
+// time (one atomic on one address per claim bounds the claim rate) while
+// large ones stay alone; the last warp out resets the counters for the next
+// launch (pv.sched[1] counts finished warps).  No waits between blocks.
 template <int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
@@ -562,14 +563,13 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
     const GatherStaged g{gsrc, xs, c0, (unsigned)S};
     const int lane = threadIdx.x & 31;
     FSum r0, r1;
-    const unsigned G = pv.claim > 1 ? (unsigned)pv.claim : 1u;
     for (;;) {
-        unsigned w0 = 0;
-        if (lane == 0) w0 = atomicAdd(pv.sched, G);
-        w0 = __shfl_sync(kFull, w0, 0);
-        if (w0 >= (unsigned)pv.nwl) break;
-        const unsigned w1 = min(w0 + G, (unsigned)pv.nwl);
-        for (unsigned w = w0; w < w1; ++w)
+        unsigned u = 0;
+        if (lane == 0) u = atomicAdd(pv.sched, 1u);
+        u = __shfl_sync(kFull, u, 0);
+        if (u >= (unsigned)pv.nunits) break;
+        const int w0 = __ldg(pv.units + u), w1 = __ldg(pv.units + u + 1);
+        for (int w = w0; w < w1; ++w)
             do_workload<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, r0, r1);
     }
     if (lane == 0) {

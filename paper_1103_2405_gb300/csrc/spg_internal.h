@@ -64,8 +64,8 @@ struct PartView {
     int32_t pf_ahead;     // bytes of a workload's slots prefetched into L2 ahead of use (0 = off)
     int32_t tma;          // 1: slots streamed into shared memory by TMA bulk copies
     int32_t persist;      // 1: persistent 8-warp blocks without an x slice
-    int32_t claim;        // persistent kernels: consecutive workloads taken per counter claim
-    int32_t pad_;
+    int32_t nunits;       // persistent kernels: claim units of this part
+    const int32_t *units; // first workload of each claim unit (nunits + 1 entries)
 };
 
 // TMA-pipelined kernel: per warp a ring of kTmaStages chunks of kTmaChunk
