@@ -126,9 +126,10 @@ typedef struct {
     /* Path of a performance table (text, see spg_load_table) or NULL for the
      * table built into the library. */
     const char *tune_table_path;
-    /* Columns of x staged in shared memory per part (the part's densest
-     * ones; the GB300 counterpart of the paper's texture-cache tile):
-     * 0 = auto (49152, i.e. 192 KB), < 0 = off (x gathered through L1/L2). */
+    /* Kernel option 1: columns of x staged in shared memory per part (the
+     * part's densest ones; the GB300 counterpart of the paper's
+     * texture-cache tile): 0 = auto (49152, i.e. 192 KB), < 0 = off (x
+     * gathered through L1/L2).  The default kernel stages none. */
     int64_t x_stage_cols;
     /* Distance, in bytes, by which each warp's bulk L2 prefetch of its slots
      * runs ahead of their use (TMA cp.async.bulk.prefetch).  <= 0 = off (the
@@ -146,13 +147,16 @@ typedef struct {
      * Algorithm 3 model sees the capped rectangles.  0 = auto (32),
      * < 0 = no cap (the paper's packing). */
     int64_t max_rows;
-    /* SpMV kernel: 0 / 1 = persistent blocks streaming slots through
-     * registers, x_stage_cols of x in shared memory (the default);
-     * 2 = plain 8-warp blocks (no shared memory); 3 = each warp streams its
-     * slots into a shared-memory ring with TMA bulk copies (24K x columns
-     * staged; measured slower at R-MAT scale 22: 0.33 ms vs 0.23 ms);
-     * 4 = persistent 8-warp blocks (five per SM, 40 warps) taking workloads
-     * from a counter, no x slice: more slot loads in flight per SM. */
+    /* SpMV kernel.  0 (default) and 4: persistent 8-warp blocks, five per SM
+     * (40 warps), taking claim units from a counter, x gathered through
+     * L1/L2; 1: one persistent 32-warp block per SM with the part's first
+     * x_stage_cols columns of x staged in shared memory (the GB300 form of
+     * the paper's texture-cache tile, Section 3.1 Solution 1); 2: plain
+     * 8-warp blocks, one workload per warp; 3: option 1 with each warp's
+     * slots streamed into a shared-memory ring by TMA bulk copies.
+     * Measured per PageRank iteration on GB300 (options 0 vs 1): R-MAT
+     * scale 22 0.213 vs 0.213 ms, R-MAT scale 26 3.64 vs 4.27 ms, Chung-Lu
+     * 50M 3.55 vs 4.05 ms; banded SpMV 0.24 vs 0.30 ms. */
     int kernel;
     /* PAGERANK handles only: store column indices alone (4 bytes per slot
      * instead of 8).  M = A^T diag(1/outdeg), so the iteration gathers

@@ -136,9 +136,8 @@ struct spg_format_t {
     } rt_fwd, rt_bwd;
     int64_t stage_cols = kStagedMaxCols;
     int32_t pf_ahead = 0;        // L2 bulk-prefetch distance of the slot stream (bytes, 0 = off)
-    int kernel = 0;              // 0/1: register stream + staged x slice, 2: plain, 3: TMA ring, 4: persistent plain
+    int kernel = 4;              // 1: staged x slice, 2: plain, 3: TMA ring, 4 (and 0): persistent plain
     int persist_blocks = 5;      // kernel 4: resident 8-warp blocks per SM
-    int64_t persist_cols = 0;    // kernel 4: x columns staged per block (0 = none)
     uint32_t *d_status = nullptr;   // set by kernels whose bounded waits ran out
     int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
     int num_sms = 152;
@@ -318,9 +317,9 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     h->pf_ahead = (h->pf_ahead + 255) / 256 * 256;
     h->loop_mode = o.loop_mode == 1 ? 1 : 0;
     h->kernel = (o.kernel >= 0 && o.kernel <= 4) ? o.kernel : 0;
-    if (o.x_stage_cols < 0 && h->kernel <= 1) h->kernel = 2;   // no shared-memory staging at all
+    if (o.x_stage_cols < 0 && h->kernel == 1) h->kernel = 2;   // no shared-memory staging at all
+    if (h->kernel == 0) h->kernel = 4;   // the default: persistent 8-warp blocks
     if (h->kernel == 4) {
-        h->persist_cols = o.x_stage_cols > 0 ? std::min<int64_t>(o.x_stage_cols, kPersistMaxCols) : 0;
         const int b = persist_blocks_per_sm();
         h->persist_blocks = b > 0 ? b : 1;
     }
@@ -708,11 +707,9 @@ static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
         pv.status = h->d_status;
         const int64_t width = ph.c1 - ph.c0;
         if (staged && h->kernel == 4 && ph.nwl_total > 0) {
-            // persistent 8-warp blocks, several per SM; an x slice per block
-            // only when x_stage_cols asks for one (each block holds its own)
+            // persistent 8-warp blocks, several per SM, no x slice
             pv.persist = 1;
-            pv.xs_cols = (h->persist_cols > 0 && width >= 1024)
-                             ? (int32_t)std::min<int64_t>(h->persist_cols, width) : 0;
+            pv.xs_cols = 0;
             pv.nblocks = (int32_t)std::min<int64_t>((int64_t)h->num_sms * h->persist_blocks,
                                                     (ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
         } else if (staged && h->kernel == 3 && !L.pattern && ph.nwl_total > 0) {

@@ -822,13 +822,10 @@ template <int MODE> static void launch_staged(const PartView &pv, const SplitVie
     if (!attr) {
         cudaFuncSetAttribute(k_part_staged<MODE, kStagedBlock, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kStagedMaxCols * (int)sizeof(float));
-        cudaFuncSetAttribute(k_part_staged<MODE, kBlock, kPersistMinBlocks>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistMaxCols * (int)sizeof(float));
         attr = true;
     }
     if (pv.persist)
-        k_part_staged<MODE, kBlock, kPersistMinBlocks><<<pv.nblocks, kBlock, (size_t)pv.xs_cols * sizeof(float), s>>>(
-            pv, sv, x, y, st, red);
+        k_part_staged<MODE, kBlock, kPersistMinBlocks><<<pv.nblocks, kBlock, 0, s>>>(pv, sv, x, y, st, red);
     else
         k_part_staged<MODE, kStagedBlock, 1><<<pv.nblocks, kStagedBlock, (size_t)pv.xs_cols * sizeof(float), s>>>(
             pv, sv, x, y, st, red);

@@ -76,8 +76,6 @@ constexpr int kTmaMaxCols = 24576;
 
 // Largest x slice staged in shared memory (floats): 192 KB.
 constexpr int kStagedMaxCols = 49152;
-// Persistent 8-warp blocks (several per SM): x columns staged per block.
-constexpr int kPersistMaxCols = 10240;
 
 // Split-row scratch shared by all parts of a format.
 struct SplitView {

@@ -38,7 +38,7 @@ def _gpu_grad(f, theta, s, t):
     return r.cpu().numpy(), dth.cpu().numpy(), info, ainfo
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(tile_width=1024, heavy_row=32), dict(kernel=4)])
+@pytest.mark.parametrize("opts", [dict(), dict(tile_width=1024, heavy_row=32), dict(kernel=1)])
 def test_weighted_rwr_and_gradient_vs_oracle(opts):
     rp, col, theta, s, t, f = _setup(11, 8, 30, opts)
     r, dth, info, ainfo = _gpu_grad(f, theta, s, t)

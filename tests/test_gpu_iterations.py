@@ -27,8 +27,8 @@ def g14():
 
 @pytest.mark.parametrize("opts", [dict(), dict(tile_width=2048), dict(tile_width=512, heavy_row=0),
                                   dict(pattern_only=True), dict(pattern_only=True, tile_width=1024),
-                                  dict(kernel=2), dict(kernel=3), dict(kernel=4),
-                                  dict(kernel=4, pattern_only=True, tile_width=4096)])
+                                  dict(kernel=2), dict(kernel=3), dict(kernel=1),
+                                  dict(kernel=1, pattern_only=True, tile_width=4096)])
 def test_pagerank_matches_oracle(g14, opts):
     rp, col, M, p_star = g14
     f = spg.Format(rp, col, kind="pagerank", **opts)
@@ -82,7 +82,7 @@ def test_pagerank_closed_forms():
 
 
 @pytest.mark.parametrize("norm", [2, 1])
-@pytest.mark.parametrize("opts", [dict(), dict(tile_width=4096, heavy_row=64), dict(kernel=4)])
+@pytest.mark.parametrize("opts", [dict(), dict(tile_width=4096, heavy_row=64), dict(kernel=1)])
 def test_hits_matches_oracle(norm, opts):
     rp, col = graphgen.rmat(13, 8, seed=1)
     a_ref, h_ref = oracle.hits(rp, col, iters=50, norm=norm)
@@ -102,7 +102,7 @@ def test_hits_golden_ratio():
     assert abs(a[3] / a[2] - phi) <= 1e-5 and abs(h[0] / h[1] - phi) <= 1e-5
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(tile_width=1024, heavy_row=32), dict(kernel=4)])
+@pytest.mark.parametrize("opts", [dict(), dict(tile_width=1024, heavy_row=32), dict(kernel=1)])
 def test_rwr_single_seed(g14, opts):
     rp, col, M, _ = g14
     s = graphgen.pick_source(rp, 3)

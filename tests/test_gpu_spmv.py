@@ -62,13 +62,13 @@ CONFIGS = [
     ("hub", dict(pattern_only=True)),
     ("rmat14", dict(kernel=2)),                                # plain 8-warp kernel
     ("rmat14", dict(kernel=3, tile_width=2048)),               # TMA ring kernel
-    ("rmat14", dict(kernel=4)),                                # flat-stream kernel
-    ("rmat14", dict(kernel=4, tile_width=2048, pattern_only=True)),
-    ("varied", dict(kernel=4)),
-    ("varied", dict(kernel=4, heavy_row=256, max_rows=-1)),
-    ("varied", dict(kernel=4, pattern_only=True, max_rows=100)),
+    ("rmat14", dict(kernel=1)),                                # staged x-slice kernel
+    ("rmat14", dict(kernel=1, tile_width=2048, pattern_only=True)),
+    ("varied", dict(kernel=1)),
+    ("varied", dict(kernel=1, heavy_row=256, max_rows=-1)),
+    ("varied", dict(kernel=1, pattern_only=True, max_rows=100)),
     ("varied", dict()),
-    ("hub", dict(kernel=4)),
+    ("hub", dict(kernel=1)),
     ("rmat14", dict(tile_width=2048)),                         # dense tiles + sparse tail
     ("rmat14", dict(tile_width=256, heavy_row=0)),             # no split rows
     ("rmat14", dict(tile_width=4096, heavy_row=32, layout_rule=0)),
