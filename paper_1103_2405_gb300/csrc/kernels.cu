@@ -14,6 +14,7 @@
 #include <atomic>
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_runtime.h>
 
@@ -181,7 +182,7 @@ __device__ __forceinline__ void epilogue(const Epi &E, uint32_t rid, float tot,
 // A chunk of a split row: publish the partial; the last chunk to arrive sums
 // all partials in chunk order and finishes the row.
 template <int MODE>
-__device__ __noinline__ void finish_split(const Epi &E, const SplitView &sv, double2 *red,
+__device__ __forceinline__ void finish_split(const Epi &E, const SplitView &sv, double2 *red,
                                           uint32_t rid, float acc, const float *__restrict__ x,
                                           float *__restrict__ y)
 {
@@ -551,16 +552,24 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
     resolve_xy<MODE>(st, x, y);
     if (MODE == EPI_ADJ) E.xs = x[E.seed];
     const float *gsrc = (MODE == EPI_PR_PAT) ? st->zbuf[st->parity] : x;
-    const int S = pv.xs_cols, c0 = pv.c0;
-    if (((c0 | S) & 3) == 0) {
-        const float4 *src = reinterpret_cast<const float4 *>(gsrc + c0);
-        float4 *dst = reinterpret_cast<float4 *>(xs);
-        for (int i = threadIdx.x; i < (S >> 2); i += blockDim.x) dst[i] = __ldg(src + i);
-    } else {
-        for (int i = threadIdx.x; i < S; i += blockDim.x) xs[i] = __ldg(gsrc + c0 + i);
+    // the 32-warp variant stages x[c0, c0 + S) in shared memory; the
+    // several-blocks-per-SM variant gathers everything through L1/L2
+    constexpr bool kStage = NT == kStagedBlock;
+    const int S = kStage ? pv.xs_cols : 0, c0 = pv.c0;
+    if (kStage) {
+        if (((c0 | S) & 3) == 0) {
+            const float4 *src = reinterpret_cast<const float4 *>(gsrc + c0);
+            float4 *dst = reinterpret_cast<float4 *>(xs);
+            for (int i = threadIdx.x; i < (S >> 2); i += blockDim.x) dst[i] = __ldg(src + i);
+        } else {
+            for (int i = threadIdx.x; i < S; i += blockDim.x) xs[i] = __ldg(gsrc + c0 + i);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    const GatherStaged g{gsrc, xs, c0, (unsigned)S};
+    using Gather = typename std::conditional<kStage, GatherStaged, GatherGlobal>::type;
+    Gather g;
+    if constexpr (kStage) g = GatherStaged{gsrc, xs, c0, (unsigned)S};
+    else g = GatherGlobal{gsrc};
     const int lane = threadIdx.x & 31;
     FSum r0, r1;
     for (;;) {
