@@ -147,9 +147,10 @@ typedef struct {
      * Algorithm 3 model sees the capped rectangles.  0 = auto (32),
      * < 0 = no cap (the paper's packing). */
     int64_t max_rows;
-    /* SpMV kernel.  0 (default) and 4: persistent 8-warp blocks, five per SM
-     * (40 warps), taking claim units from a counter, x gathered through
-     * L1/L2; 1: one persistent 32-warp block per SM with the part's first
+    /* SpMV kernel.  0 (default) and 4: persistent 8-warp blocks -- five per
+     * SM (40 warps) for plain SpMV, four (32 warps, no register spills) for
+     * the fused power-iteration epilogues -- taking claim units from a
+     * counter, x gathered through L1/L2; 1: one persistent 32-warp block per SM with the part's first
      * x_stage_cols columns of x staged in shared memory (the GB300 form of
      * the paper's texture-cache tile, Section 3.1 Solution 1); 2: plain
      * 8-warp blocks, one workload per warp; 3: option 1 with each warp's

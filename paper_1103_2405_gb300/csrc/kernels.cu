@@ -48,10 +48,15 @@ constexpr int kStagedBlock = 1024;
 // Persistent plain variant: 8-warp blocks, kPersistMinBlocks per SM, no x
 // slice -- more resident warps (more slot loads in flight) than the staged
 // kernel's one 32-warp block.
-#ifndef SPG_PERSIST_MINB
-#define SPG_PERSIST_MINB 5
-#endif
-constexpr int kPersistMinBlocks = SPG_PERSIST_MINB;
+// Blocks per SM: 5 (48 registers) for the plain SpMV, whose loop needs no
+// more; 4 (64 registers, no spills) for the power-iteration epilogues --
+// measured best for each (R-MAT 22 PageRank iteration 0.192 ms at 4 vs
+// 0.198 at 5; banded SpMV 0.230 ms at 5 vs 0.240 at 4).
+constexpr int kPersistMinBlocks = 5;
+__host__ __device__ constexpr int persist_minb(int mode)
+{
+    return (mode == EPI_RAW || mode == EPI_RAW_PAT) ? kPersistMinBlocks : 4;
+}
 
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -809,7 +814,7 @@ template <int MODE> static void launch_tma(const PartView &pv, const SplitView &
 int persist_blocks_per_sm()
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_part_staged<EPI_PAGERANK, kBlock, kPersistMinBlocks>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_part_staged<EPI_RAW, kBlock, kPersistMinBlocks>,
                                                       kBlock, 0) != cudaSuccess)
         return 0;
     return b;
@@ -834,7 +839,7 @@ template <int MODE> static void launch_staged(const PartView &pv, const SplitVie
         attr = true;
     }
     if (pv.persist)
-        k_part_staged<MODE, kBlock, kPersistMinBlocks><<<pv.nblocks, kBlock, 0, s>>>(pv, sv, x, y, st, red);
+        k_part_staged<MODE, kBlock, persist_minb(MODE)><<<pv.nblocks, kBlock, 0, s>>>(pv, sv, x, y, st, red);
     else
         k_part_staged<MODE, kStagedBlock, 1><<<pv.nblocks, kStagedBlock, (size_t)pv.xs_cols * sizeof(float), s>>>(
             pv, sv, x, y, st, red);
