@@ -181,6 +181,11 @@ typedef struct {
      * claim bounds the claim rate, which small workloads would otherwise
      * hit.  0 = auto (2048), 1 = one workload per claim. */
     int64_t unit_slots;
+    /* Power iterations: 0 = the convergence check (fixed-order sums of the
+     * block partials, state update, graph condition) runs in the last block
+     * of each iteration's last part kernel; 1 = in a one-block kernel of its
+     * own after the parts (one more launch per iteration). */
+    int32_t separate_check;
 } spg_build_opts;
 
 /* Per-call results of the power iterations. */

@@ -46,7 +46,7 @@ class _Opts(ctypes.Structure):
                 ("slab_prefetch", ctypes.c_int64), ("loop_mode", ctypes.c_int),
                 ("max_rows", ctypes.c_int64), ("kernel", ctypes.c_int), ("pattern_only", ctypes.c_int),
                 ("row_part", ctypes.c_void_p), ("part_id", ctypes.c_int32), ("nparts", ctypes.c_int32),
-                ("unit_slots", ctypes.c_int64)]
+                ("unit_slots", ctypes.c_int64), ("separate_check", ctypes.c_int32)]
 
 
 class IterInfo(ctypes.Structure):
@@ -203,7 +203,8 @@ class Format:
                  layout_rule=1, max_warps=0, vec_width=1, build_transpose=False, keep_plan=False,
                  keep_csr=False, host_only=False, split_cost=0.0, table=None, x_stage_cols=0,
                  slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, pattern_only=False,
-                 row_part=None, part_id=0, nparts=None, unit_slots=0, stream=None):
+                 row_part=None, part_id=0, nparts=None, unit_slots=0, separate_check=False,
+                 stream=None):
         L = lib()
         self._h = ctypes.c_void_p(None)
         on_dev = _is_torch(rowptr) and rowptr.is_cuda
@@ -226,6 +227,7 @@ class Format:
                      int(slab_prefetch), int(loop_mode), int(max_rows), int(kernel),
                      int(bool(pattern_only)))
         opts.unit_slots = int(unit_slots)
+        opts.separate_check = int(bool(separate_check))
         if row_part is not None:
             row_part = np.ascontiguousarray(row_part, dtype=np.int32)
             opts.row_part = row_part.ctypes.data

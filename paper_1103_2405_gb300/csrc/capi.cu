@@ -140,6 +140,7 @@ struct spg_format_t {
     int persist_blocks = 5;      // kernel 4: resident 8-warp blocks per SM
     uint32_t *d_status = nullptr;   // set by kernels whose bounded waits ran out
     int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
+    bool separate_check = false; // convergence check in its own kernel (not fused)
     int num_sms = 152;
     std::map<std::string, LoopGraph> graphs;
     LoopGraph host_loop;         // loop_mode 1
@@ -316,6 +317,7 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     h->pf_ahead = o.slab_prefetch > 0 ? (int32_t)std::min<int64_t>(o.slab_prefetch, 1 << 20) : 0;
     h->pf_ahead = (h->pf_ahead + 255) / 256 * 256;
     h->loop_mode = o.loop_mode == 1 ? 1 : 0;
+    h->separate_check = o.separate_check != 0;
     h->kernel = (o.kernel >= 0 && o.kernel <= 4) ? o.kernel : 0;
     if (o.x_stage_cols < 0 && h->kernel == 1) h->kernel = 2;   // no shared-memory staging at all
     if (h->kernel == 0) h->kernel = 4;   // the default: persistent 8-warp blocks
@@ -325,8 +327,8 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     }
     CK(cudaMalloc((void **)&h->d_status, sizeof(uint32_t)));
     CK(cudaMemset(h->d_status, 0, sizeof(uint32_t)));
-    CK(h->rt_fwd.sched.ensure(2 * h->fwd.parts.size()));
-    CK(cudaMemset(h->rt_fwd.sched.p, 0, 2 * h->fwd.parts.size() * sizeof(uint32_t)));
+    CK(h->rt_fwd.sched.ensure(2 * h->fwd.parts.size() + 1));
+    CK(cudaMemset(h->rt_fwd.sched.p, 0, (2 * h->fwd.parts.size() + 1) * sizeof(uint32_t)));
     CK(cudaMalloc((void **)&h->d_state, sizeof(IterState)));
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
@@ -516,8 +518,8 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
                     if (!build_layout(ts, prm, *h->bwd, err)) return fail(SPG_ERR_INVALID, err);
                     cudaError_t e = upload_layout(*h->bwd, o.keep_plan != 0, s);
                     if (e != cudaSuccess) return cuda_fail(e, "upload transpose");
-                    CK(h->rt_bwd.sched.ensure(2 * h->bwd->parts.size()));
-                    CK(cudaMemset(h->rt_bwd.sched.p, 0, 2 * h->bwd->parts.size() * sizeof(uint32_t)));
+                    CK(h->rt_bwd.sched.ensure(2 * h->bwd->parts.size() + 1));
+                    CK(cudaMemset(h->rt_bwd.sched.p, 0, (2 * h->bwd->parts.size() + 1) * sizeof(uint32_t)));
                 }
             }
         }
@@ -788,6 +790,35 @@ static void launch_parts(spg_handle h, int mode, const float *x, float *y, const
     for (const PartView &pv : V.v) launch_part(mode, pv, sv, x, y, st, red, s);
 }
 
+// One power iteration: the parts' kernels, then the convergence check --
+// fused into the last part's kernel (its last block) when that kernel
+// supports it, else the one-block check kernel.  check_mode is the form of
+// the check (PageRank form for PageRank, RWR and the adjoint; HITS form).
+static void launch_iteration(spg_handle h, const Layout &L, spg_format_t::LayoutRT &rt, int mode,
+                             int check_mode, int nred, unsigned long long cond, int uc, cudaStream_t cs)
+{
+    const spg_format_t::Views &V = get_views_L(h, L, rt, true);
+    const SplitView sv = split_of_L(L, V);
+    if (L.pattern) mode = mode == EPI_RAW ? EPI_RAW_PAT : (mode == EPI_PAGERANK ? EPI_PR_PAT : mode);
+    int last = -1;
+    for (size_t p = 0; p < V.v.size(); ++p)
+        if (V.v[p].nblocks > 0) last = (int)p;
+    bool fused = false;
+    for (size_t p = 0; p < V.v.size(); ++p) {
+        FuseCheck fc;
+        if ((int)p == last && !h->separate_check && nred > 0) {
+            fc.cond = cond;
+            fc.use_cond = uc;
+            fc.nred = nred;
+            fc.st = h->d_state;
+            fc.done = rt.sched.p + 2 * L.parts.size();
+        }
+        const bool f = launch_part(mode, V.v[p], sv, nullptr, nullptr, h->d_state, h->red.p, cs, fc);
+        if ((int)p == last) fused = f;
+    }
+    if (!fused) launch_check(check_mode, h->d_state, h->red.p, nred, cond, uc, cs);
+}
+
 extern "C" spg_status spg_spmv_permuted(spg_handle h, const float *xp, float *yp, void *stream)
 {
     if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
@@ -1013,8 +1044,7 @@ extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int 
     LoopGraph *g;
     const int nred = nred_of(h, get_views(h, true));
     st = get_loop_graph(h, pat ? "pagerank_pattern" : "pagerank", [&](cudaStream_t cs, unsigned long long cond, int uc) {
-        launch_parts(h, EPI_PAGERANK, nullptr, nullptr, h->d_state, h->red.p, cs);
-        launch_check(EPI_PAGERANK, h->d_state, h->red.p, nred, cond, uc, cs);
+        launch_iteration(h, h->fwd, h->rt_fwd, EPI_PAGERANK, EPI_PAGERANK, nred, cond, uc, cs);
     }, &g);
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
@@ -1046,8 +1076,7 @@ extern "C" spg_status spg_hits(spg_handle h, int norm, double tol, int max_iter,
     LoopGraph *g;
     const int nred = nred_of(h, get_views(h, true));
     st = get_loop_graph(h, "hits", [&](cudaStream_t cs, unsigned long long cond, int uc) {
-        launch_parts(h, EPI_HITS, nullptr, nullptr, h->d_state, h->red.p, cs);
-        launch_check(EPI_HITS, h->d_state, h->red.p, nred, cond, uc, cs);
+        launch_iteration(h, h->fwd, h->rt_fwd, EPI_HITS, EPI_HITS, nred, cond, uc, cs);
     }, &g);
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
@@ -1098,8 +1127,7 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
         CK(h->init_part.ensure((size_t)init_delta_scratch()));
         launch_init_delta(h->d_state, h->init_part.p, s);
         st = get_loop_graph(h, "rwr1", [&](cudaStream_t cs, unsigned long long cond, int uc) {
-            launch_parts(h, EPI_RWR, nullptr, nullptr, h->d_state, h->red.p, cs);
-            launch_check(EPI_RWR, h->d_state, h->red.p, nred, cond, uc, cs);
+            launch_iteration(h, h->fwd, h->rt_fwd, EPI_RWR, EPI_RWR, nred, cond, uc, cs);
         }, &g);
         if (st != SPG_OK) return st;
         CK(cudaGetLastError());
@@ -1497,8 +1525,7 @@ extern "C" spg_status spg_rwr_adjoint(spg_handle h, float restart, int32_t seed,
     CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
     LoopGraph *lg;
     st = get_loop_graph(h, "adjoint", [&](cudaStream_t cs, unsigned long long cond, int uc) {
-        launch_parts_L(h, Lb, h->rt_bwd, EPI_ADJ, h->d_state, h->red.p, cs);
-        launch_check(EPI_PAGERANK, h->d_state, h->red.p, nred, cond, uc, cs);
+        launch_iteration(h, Lb, h->rt_bwd, EPI_ADJ, EPI_PAGERANK, nred, cond, uc, cs);
     }, &lg);
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());

@@ -318,6 +318,78 @@ __device__ __forceinline__ void block_reduce_store(const FSum &f0, const FSum &f
     }
 }
 
+__device__ __forceinline__ void block_sum2_1024(double &a, double &b)
+{
+    __shared__ double s0[32], s1[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    if (lane == 0) { s0[warp] = a; s1[warp] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) { x += s0[w]; y += s1[w]; }
+        a = x;
+        b = y;
+    }
+}
+
+// The convergence check of one iteration (fixed-order sums of the block
+// partials, then the state update and the graph loop's condition), run by
+// one block: the check kernel, or the last block of the iteration's last
+// part kernel (fused).
+__device__ __forceinline__ void check_body(int mode, IterState *st, const double2 *red, int nred,
+                                           cudaGraphConditionalHandle cond, int use_cond)
+{
+    if (st->done) return;   // host-loop mode may launch past convergence
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nred; i += blockDim.x) {
+        const double2 v = red[i];
+        a += v.x;
+        b += v.y;
+    }
+    block_sum2_1024(a, b);
+    if (threadIdx.x == 0) {
+        if (mode == EPI_HITS) {
+            const double na = st->hits_norm == 2 ? sqrt(a) : a;
+            const double nh = st->hits_norm == 2 ? sqrt(b) : b;
+            st->scale[0] = na > 0.0 ? 1.0 / na : 0.0;
+            st->scale[1] = nh > 0.0 ? 1.0 / nh : 0.0;
+            st->l1 = 0.0;
+        } else {
+            st->l1 = a;
+            st->delta = b;
+        }
+        st->iter += 1;
+        st->parity ^= 1;
+        const int done = st->iter >= st->max_iter ||
+                         (mode != EPI_HITS && st->tol > 0.0 && st->l1 < st->tol);
+        st->done = done;
+        if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
+    }
+}
+
+// Fused check: after its block partial is stored, each block of the
+// iteration's last part kernel counts itself out; the last one -- every
+// other block of this launch and every earlier launch of the iteration has
+// then written its partials -- runs the check and re-arms the counter.
+template <int MODE>
+__device__ __forceinline__ void fused_check(const FuseCheck &fc, const double2 *red)
+{
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(fc.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    check_body(MODE == EPI_PR_PAT ? EPI_PAGERANK : MODE, fc.st, red, fc.nred,
+               (cudaGraphConditionalHandle)fc.cond, fc.use_cond);
+    if (threadIdx.x == 0) *fc.done = 0u;
+}
+
 // x gathers: straight from global memory through the read-only path, or
 // from the shared-memory copy of the part's first `S` columns (its densest
 // ones: columns are in decreasing-length order) with global fallback.
@@ -547,8 +619,7 @@ k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restri
 template <int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
-              float *__restrict__ yout, const IterState *__restrict__ st,
-              double2 *__restrict__ red)
+              float *__restrict__ yout, const IterState *st, double2 *red, FuseCheck fc)
 {
     extern __shared__ float xs[];
     const float *x = xin;
@@ -593,7 +664,10 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
             pv.sched[1] = 0u;
         }
     }
-    if (MODE != EPI_RAW && MODE != EPI_RAW_PAT && MODE != EPI_BATCH) block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
+    if (MODE != EPI_RAW && MODE != EPI_RAW_PAT && MODE != EPI_BATCH) {
+        block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
+        if (fc.nred > 0) fused_check<MODE>(fc, red);
+    }
 }
 
 // ------------------------------------------------ TMA-pipelined kernel --
@@ -830,7 +904,7 @@ int part_blocks_per_sm()
 
 template <int MODE> static void launch_staged(const PartView &pv, const SplitView &sv, const float *x,
                                               float *y, const IterState *st, double2 *red,
-                                              cudaStream_t s)
+                                              const FuseCheck &fc, cudaStream_t s)
 {
     static bool attr = false;
     if (!attr) {
@@ -839,16 +913,16 @@ template <int MODE> static void launch_staged(const PartView &pv, const SplitVie
         attr = true;
     }
     if (pv.persist)
-        k_part_staged<MODE, kBlock, persist_minb(MODE)><<<pv.nblocks, kBlock, 0, s>>>(pv, sv, x, y, st, red);
+        k_part_staged<MODE, kBlock, persist_minb(MODE)><<<pv.nblocks, kBlock, 0, s>>>(pv, sv, x, y, st, red, fc);
     else
         k_part_staged<MODE, kStagedBlock, 1><<<pv.nblocks, kStagedBlock, (size_t)pv.xs_cols * sizeof(float), s>>>(
-            pv, sv, x, y, st, red);
+            pv, sv, x, y, st, red, fc);
 }
 
-void launch_part(int mode, const PartView &pv, const SplitView &sv, const float *x, float *y,
-                 const IterState *st, double2 *red, cudaStream_t s)
+bool launch_part(int mode, const PartView &pv, const SplitView &sv, const float *x, float *y,
+                 const IterState *st, double2 *red, cudaStream_t s, const FuseCheck &fc)
 {
-    if (pv.nblocks <= 0) return;
+    if (pv.nblocks <= 0) return false;
     if (pv.tma) {
         switch (mode) {
         case EPI_RAW: launch_tma<EPI_RAW>(pv, sv, x, y, st, red, s); break;
@@ -859,21 +933,21 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
         default: launch_tma<EPI_HITS>(pv, sv, x, y, st, red, s); break;
         }
         count_launches(1);
-        return;
+        return false;
     }
     if (pv.xs_cols > 0 || pv.persist) {
         switch (mode) {
-        case EPI_RAW: launch_staged<EPI_RAW>(pv, sv, x, y, st, red, s); break;
-        case EPI_PAGERANK: launch_staged<EPI_PAGERANK>(pv, sv, x, y, st, red, s); break;
-        case EPI_RWR: launch_staged<EPI_RWR>(pv, sv, x, y, st, red, s); break;
-        case EPI_ADJ: launch_staged<EPI_ADJ>(pv, sv, x, y, st, red, s); break;
-        case EPI_BATCH: launch_staged<EPI_BATCH>(pv, sv, x, y, st, red, s); break;
-        case EPI_PR_PAT: launch_staged<EPI_PR_PAT>(pv, sv, x, y, st, red, s); break;
-        case EPI_RAW_PAT: launch_staged<EPI_RAW_PAT>(pv, sv, x, y, st, red, s); break;
-        default: launch_staged<EPI_HITS>(pv, sv, x, y, st, red, s); break;
+        case EPI_RAW: launch_staged<EPI_RAW>(pv, sv, x, y, st, red, fc, s); break;
+        case EPI_PAGERANK: launch_staged<EPI_PAGERANK>(pv, sv, x, y, st, red, fc, s); break;
+        case EPI_RWR: launch_staged<EPI_RWR>(pv, sv, x, y, st, red, fc, s); break;
+        case EPI_ADJ: launch_staged<EPI_ADJ>(pv, sv, x, y, st, red, fc, s); break;
+        case EPI_BATCH: launch_staged<EPI_BATCH>(pv, sv, x, y, st, red, fc, s); break;
+        case EPI_PR_PAT: launch_staged<EPI_PR_PAT>(pv, sv, x, y, st, red, fc, s); break;
+        case EPI_RAW_PAT: launch_staged<EPI_RAW_PAT>(pv, sv, x, y, st, red, fc, s); break;
+        default: launch_staged<EPI_HITS>(pv, sv, x, y, st, red, fc, s); break;
         }
         count_launches(1);
-        return;
+        return fc.nred > 0 && mode != EPI_RAW && mode != EPI_RAW_PAT && mode != EPI_BATCH;
     }
     dim3 g(pv.nblocks), b(kBlock);
     switch (mode) {
@@ -887,6 +961,7 @@ void launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
     default: k_part<EPI_HITS><<<g, b, 0, s>>>(pv, sv, x, y, st, red); break;
     }
     count_launches(1);
+    return false;
 }
 
 // ------------------------------------------------------------------ SpMM --
@@ -1294,53 +1369,11 @@ void launch_part_spmm(int mode, const PartView &pv, const SplitView &sv, const f
 
 // ----------------------------------------------------------------- check --
 
-__device__ __forceinline__ void block_sum2_1024(double &a, double &b)
-{
-    __shared__ double s0[32], s1[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    a = warp_sum_d(a);
-    b = warp_sum_d(b);
-    if (lane == 0) { s0[warp] = a; s1[warp] = b; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double x = 0.0, y = 0.0;
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int w = 0; w < nw; ++w) { x += s0[w]; y += s1[w]; }
-        a = x;
-        b = y;
-    }
-}
-
 __global__ void __launch_bounds__(1024)
 k_check(int mode, IterState *st, const double2 *__restrict__ red, int nred,
         cudaGraphConditionalHandle cond, int use_cond)
 {
-    if (st->done) return;   // host-loop mode may launch past convergence
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < nred; i += blockDim.x) {
-        const double2 v = red[i];
-        a += v.x;
-        b += v.y;
-    }
-    block_sum2_1024(a, b);
-    if (threadIdx.x == 0) {
-        if (mode == EPI_HITS) {
-            const double na = st->hits_norm == 2 ? sqrt(a) : a;
-            const double nh = st->hits_norm == 2 ? sqrt(b) : b;
-            st->scale[0] = na > 0.0 ? 1.0 / na : 0.0;
-            st->scale[1] = nh > 0.0 ? 1.0 / nh : 0.0;
-            st->l1 = 0.0;
-        } else {
-            st->l1 = a;
-            st->delta = b;
-        }
-        st->iter += 1;
-        st->parity ^= 1;
-        const int done = st->iter >= st->max_iter ||
-                         (mode != EPI_HITS && st->tol > 0.0 && st->l1 < st->tol);
-        st->done = done;
-        if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
-    }
+    check_body(mode, st, red, nred, cond, use_cond);
 }
 
 void launch_check(int mode, IterState *st, const double2 *red, int nred,

@@ -20,8 +20,20 @@ enum EpiMode {
 
 // One tiled-composite launch of one part (Solution 3: one warp per
 // workload).  x/y come from st->buf[parity] when st != nullptr.
-void launch_part(int mode, const PartView &pv, const SplitView &sv, const float *x, float *y,
-                 const IterState *st, double2 *red, cudaStream_t s);
+// Fused convergence check: when nred > 0, the last block of the launch runs
+// the iteration's check over red[0, nred) on st (and the graph condition).
+struct FuseCheck {
+    unsigned long long cond = 0;
+    unsigned *done = nullptr;     // arrival counter, zero between launches
+    IterState *st = nullptr;
+    int use_cond = 0;
+    int nred = 0;
+};
+
+// Returns true if the launch also ran the check (fc.nred > 0 and a kernel
+// that supports it).
+bool launch_part(int mode, const PartView &pv, const SplitView &sv, const float *x, float *y,
+                 const IterState *st, double2 *red, cudaStream_t s, const FuseCheck &fc = FuseCheck());
 
 // SpMM over one part: Y' (n x k, ld k) += rows of M' X' (k <= 1024).  Modes
 // EPI_RAW and EPI_RWR (per-column restart seeds, per-column sums into

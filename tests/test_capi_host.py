@@ -149,7 +149,7 @@ def test_malformed_csr_rejected(spg, bad):
         col = np.array([1, 2, 0, 0], np.int32)
     csr = spg._Csr(n, nc, nnz, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(col.ctypes.data),
                    None, 0)
-    opts = spg._Opts(0, 0, -1, 1, 64, 1, 0, 0, 0, -1, 0.0, None, 0, 0, 0, 0, 0, 0, None, 0, 0, 0)
+    opts = spg._Opts(0, 0, -1, 1, 64, 1, 0, 0, 0, -1, 0.0, None, 0, 0, 0, 0, 0, 0, None, 0, 0, 0, 0)
     h = ctypes.c_void_p()
     st = L.spg_build_format(ctypes.byref(csr), 1, ctypes.byref(opts), None, ctypes.byref(h))
     assert st == -1 and not h.value
