@@ -39,6 +39,10 @@ WORKLOADS = {
                           "average degree 12, one batched PageRank iteration"),
     "adjoint20": dict(scale=20, ef=16, desc="R-MAT scale 20, edge factor 16, softmax edge "
                                             "weights, one adjoint (transposed SpMV) iteration"),
+    "hits22": dict(scale=22, ef=16, desc="R-MAT scale 22, edge factor 16, HITS (L2-normalised "
+                                          "halves) iteration on the 2n x 2n block matrix"),
+    "rwr22": dict(scale=22, ef=16, desc="R-MAT scale 22, edge factor 16, single-source RWR "
+                                         "(restart 0.15) iteration"),
     "dense2k": dict(desc="dense 2048 x 2048 matrix, every entry stored, one SpMV (the paper's "
                          "dense sanity case)"),
     "banded": dict(desc="banded 8,388,608 x 8,388,608, half-bandwidth 8 (17 entries per row), "
@@ -245,6 +249,51 @@ def run_secondary(args):
                  "e2e": {"value": e2e_v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                          "d2h_bytes_per_step": 4 * 64 * n}}
         value = flops / (ms * 1e-3) / 1e9
+    elif args.workload in ("hits22", "rwr22"):
+        rp, col = graph(args.workload)
+        n, nnz = int(rp.shape[0] - 1), int(rp[-1])
+        hits = args.workload == "hits22"
+        f = spg.Format(rp, col, kind="hits" if hits else "pagerank")
+        s = graphgen.pick_source(rp, 3)
+        if hits:
+            run = lambda k: f.hits(norm=2, iters=k, like=like)
+            flops_it = 2.0 * 2 * nnz       # both halves: A^T h and A a
+            alg = 2 * (8 * nnz) + 16 * 2 * n
+        else:
+            run = lambda k: f.rwr([s], 0.15, tol=0.0, max_iter=k, like=like)
+            flops_it = 2.0 * nnz
+            alg = 8 * nnz + 16 * n
+        run(args.warmup)
+        L0 = spg.launch_count()
+        with Clocks(0) as clk:
+            t = timed(lambda: run(args.steps), dev)
+        ms = t / args.steps
+        value = flops_it / (ms * 1e-3) / 1e9
+        if hits:
+            full = timed(lambda: f.hits(norm=2, iters=50, like=like), dev)
+            solve = {"hits_50_iterations_ms": full}
+            hout = (torch.empty(n).pin_memory(), torch.empty(n).pin_memory())
+            t1 = time.perf_counter()
+            f.hits(norm=2, iters=50, auth=hout[0], hub=hout[1])
+            e2e_v = flops_it * 50 / (time.perf_counter() - t1) / 1e9
+            d2h = 8 * n
+        else:
+            full = timed(lambda: f.rwr([s], 0.15, tol=1e-8, max_iter=1000, like=like), dev)
+            solve = {"solve_ms_tol_1e-8": full}
+            hout = torch.empty(n).pin_memory()
+            t1 = time.perf_counter()
+            _, inf = f.rwr([s], 0.15, tol=1e-8, max_iter=1000, out=hout)
+            e2e_v = flops_it * inf["iters"] / (time.perf_counter() - t1) / 1e9
+            d2h = 4 * n
+        info = f.info()
+        cfg = {"workload": w["desc"], "n": n, "nnz": nnz, "parts": info["ntile"] + 1, **solve,
+               "l2": "inputs larger than L2"}
+        extra = {"roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
+                              "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None,
+                              "kernel": ("k_part_staged<EPI_HITS>" if hits else "k_part_staged<EPI_RWR>")
+                                        + " (fused epilogue and check)"},
+                 "e2e": {"value": e2e_v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                         "d2h_bytes_per_step": d2h}}
     elif args.workload == "batch512":
         graphs = batch_graphs(512)
         nnz = sum(int(g[0][-1]) for g in graphs)
@@ -400,7 +449,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    if args.workload in ("rwr64", "batch512", "adjoint20") + UNSTRUCTURED:
+    if args.workload in ("rwr64", "batch512", "adjoint20", "hits22", "rwr22") + UNSTRUCTURED:
         print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm times the "
                           "PageRank workloads only"}), flush=True)
         return
@@ -430,7 +479,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("rwr64", "batch512", "adjoint20"):
+    if args.workload in ("rwr64", "batch512", "adjoint20", "hits22", "rwr22"):
         return run_secondary(args)
     if args.workload in UNSTRUCTURED:
         return run_unstructured(args)
