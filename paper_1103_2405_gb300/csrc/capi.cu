@@ -773,13 +773,6 @@ static spg_status device_in(spg_handle h, const float *p, int64_t count, const f
     return SPG_OK;
 }
 
-static void launch_parts_L(spg_handle h, const Layout &L, spg_format_t::LayoutRT &rt, int mode,
-                           const IterState *st, double2 *red, cudaStream_t s)
-{
-    const spg_format_t::Views &V = get_views_L(h, L, rt, true);
-    const SplitView sv = split_of_L(L, V);
-    for (const PartView &pv : V.v) launch_part(mode, pv, sv, nullptr, nullptr, st, red, s);
-}
 
 static void launch_parts(spg_handle h, int mode, const float *x, float *y, const IterState *st,
                          double2 *red, cudaStream_t s)
