@@ -26,6 +26,7 @@ using namespace spg;
 
 // Default cap on the rows of one workload (spg_build_opts.max_rows = 0).
 static constexpr int64_t kDefaultUnitSlots = 2048;   // claim unit cost (measured)
+static constexpr int64_t kBatchChunk = 8192;         // positions per chunk of the per-graph sums
 static constexpr int64_t kDefaultMaxRows = 32;
 
 static thread_local std::string g_err;
@@ -108,6 +109,10 @@ struct spg_format_t {
     int32_t *d_gid = nullptr, *d_giters = nullptr;
     float *d_gbase = nullptr;
     double *d_gl1 = nullptr, *d_gdelta = nullptr;
+    int nchunk = 0;                  // fixed position chunks of the per-graph sums
+    int64_t *d_cstart = nullptr;
+    int32_t *d_cgraph = nullptr, *d_gchunk = nullptr;
+    double2 *d_cpart = nullptr;
     // WEIGHTED: A on the device and the current transition weights
     int64_t *d_arp = nullptr;
     int32_t *d_acol = nullptr;
@@ -179,6 +184,7 @@ struct spg_format_t {
         cudaFree(d_goff); cudaFree(d_gdstart); cudaFree(d_gid); cudaFree(d_giters);
         cudaFree(d_status);
         cudaFree(d_gbase); cudaFree(d_gl1); cudaFree(d_gdelta);
+        cudaFree(d_cstart); cudaFree(d_cgraph); cudaFree(d_gchunk); cudaFree(d_cpart);
         x.release(); y.release(); stage_in.release(); stage_out.release(); red.release();
         rt_fwd.sched.release();
         rt_bwd.sched.release();
@@ -1631,6 +1637,23 @@ extern "C" spg_status spg_build_batch(const spg_csr *graphs, int count,
             CK(cudaMalloc((void **)&h->d_gbase, count * sizeof(float)));
             CK(cudaMalloc((void **)&h->d_gl1, count * sizeof(double)));
             CK(cudaMalloc((void **)&h->d_gdelta, count * sizeof(double)));
+            // per-graph sums in fixed chunks of at most kBatchChunk positions
+            std::vector<int64_t> cstart;
+            std::vector<int32_t> cgraph, gchunk((size_t)count + 1);
+            for (int g = 0; g < count; ++g) {
+                gchunk[(size_t)g] = (int32_t)cgraph.size();
+                for (int64_t v = h->goff[(size_t)g]; v < h->goff[(size_t)g + 1]; v += kBatchChunk) {
+                    cstart.push_back(v);
+                    cgraph.push_back(g);
+                }
+            }
+            gchunk[(size_t)count] = (int32_t)cgraph.size();
+            cstart.push_back(N);
+            h->nchunk = (int)cgraph.size();
+            CK(upload(&h->d_cstart, cstart.data(), cstart.size()));
+            CK(upload(&h->d_cgraph, cgraph.data(), cgraph.size()));
+            CK(upload(&h->d_gchunk, gchunk.data(), gchunk.size()));
+            CK(cudaMalloc((void **)&h->d_cpart, std::max(1, h->nchunk) * sizeof(double2)));
         }
         *out = h.release();
         return SPG_OK;
@@ -1669,6 +1692,11 @@ extern "C" spg_status spg_batch_pagerank(spg_handle h, float damping, double tol
     hs.goff = h->d_goff;
     hs.gdstart = h->d_gdstart;
     hs.ngraph = G;
+    hs.nchunk = h->nchunk;
+    hs.cstart = h->d_cstart;
+    hs.cgraph = h->d_cgraph;
+    hs.gchunk = h->d_gchunk;
+    hs.cpart = h->d_cpart;
     CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(h->d_giters, 0, G * sizeof(int32_t), s));
     // p(0) = 1/n_g: its dangling mass is (#dangling_g)/n_g
@@ -1683,7 +1711,7 @@ extern "C" spg_status spg_batch_pagerank(spg_handle h, float damping, double tol
     LoopGraph *lg;
     st = get_loop_graph(h, "batch", [&](cudaStream_t cs, unsigned long long cond, int uc) {
         launch_parts(h, EPI_BATCH, nullptr, nullptr, h->d_state, h->red.p, cs);
-        launch_batch_reduce(h->d_state, G, cs);
+        launch_batch_reduce(h->d_state, h->nchunk, cs);
         launch_batch_check(h->d_state, G, cond, uc, cs);
     }, &lg);
     if (st != SPG_OK) return st;

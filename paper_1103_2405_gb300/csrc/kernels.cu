@@ -1610,13 +1610,19 @@ void launch_init_delta_k(int64_t dangling_start, int64_t n, const float *X, int 
 
 // Block g: L1 change and dangling mass of graph g over its positions
 // [goff[g], goff[g+1]) (its dangling tail starts at gdstart[g]); fixed order.
-__global__ void __launch_bounds__(256) k_batch_reduce(IterState *st)
+// Per-graph L1 change and dangling mass, stage 1: block c sums chunk c --
+// a fixed range of at most kBatchChunk positions of one graph -- (each
+// thread a fixed strided subset, TwoSum pairs, then the warps in order) into
+// cpart[c].  The check adds each graph's chunks in order (stage 2).
+__global__ void __launch_bounds__(256) k_batch_reduce(const IterState *st)
 {
-    const int g = blockIdx.x;
+    const int c = blockIdx.x;
     const float *x = st->buf[st->parity];
     const float *y = st->buf[st->parity ^ 1];
-    const int64_t a = st->goff[g], b = st->goff[g + 1], ds = st->gdstart[g];
+    const int g = st->cgraph[c];
+    const int64_t a = st->cstart[c], b = st->cstart[c + 1], ds = st->gdstart[g];
     FSum fl1, fdg;
+#pragma unroll 4
     for (int64_t v = a + threadIdx.x; v < b; v += blockDim.x) {
         const float f = y[v];
         fl1.add(fabsf(f - x[v]));
@@ -1631,14 +1637,13 @@ __global__ void __launch_bounds__(256) k_batch_reduce(IterState *st)
     if (threadIdx.x == 0) {
         double p = 0.0, q = 0.0;
         for (int w = 0; w < 8; ++w) { p += s0[w]; q += s1[w]; }
-        st->gl1[g] = p;
-        st->gdelta[g] = q;
+        st->cpart[c] = make_double2(p, q);
     }
 }
 
-void launch_batch_reduce(IterState *st, int ngraph, cudaStream_t s)
+void launch_batch_reduce(IterState *st, int nchunk, cudaStream_t s)
 {
-    k_batch_reduce<<<ngraph, 256, 0, s>>>(st);
+    k_batch_reduce<<<nchunk, 256, 0, s>>>(st);
     count_launches(1);
 }
 
@@ -1656,9 +1661,16 @@ __global__ void __launch_bounds__(1024) k_batch_check(IterState *st, int ngraph,
     double mx = 0.0;
     int all = 1;
     for (int g = threadIdx.x; g < ngraph; g += blockDim.x) {
-        const double l1 = st->gl1[g];
+        double l1 = 0.0, dg = 0.0;
+        for (int q = st->gchunk[g]; q < st->gchunk[g + 1]; ++q) {
+            const double2 v = st->cpart[q];
+            l1 += v.x;
+            dg += v.y;
+        }
+        st->gl1[g] = l1;
+        st->gdelta[g] = dg;
         const double ng = (double)(st->goff[g + 1] - st->goff[g]);
-        st->gbase[g] = (float)((c * st->gdelta[g] + (1.0 - c)) / ng);
+        st->gbase[g] = (float)((c * dg + (1.0 - c)) / ng);
         if (tol > 0.0 && l1 < tol) {
             if (st->giters[g] == 0) st->giters[g] = it;
         } else {

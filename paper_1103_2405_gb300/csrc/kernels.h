@@ -120,7 +120,7 @@ int part_blocks_per_sm();
 // Batch of graphs: per-graph L1 change and dangling mass (one block per
 // graph, fixed order), then the per-graph bases, convergence record and the
 // loop condition (one block).
-void launch_batch_reduce(IterState *st, int ngraph, cudaStream_t s);
+void launch_batch_reduce(IterState *st, int nchunk, cudaStream_t s);
 void launch_batch_check(IterState *st, int ngraph, unsigned long long cond, int use_cond,
                         cudaStream_t s);
 // x[v] = 1 / n_{graph of v}

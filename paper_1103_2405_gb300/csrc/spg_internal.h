@@ -117,7 +117,11 @@ struct IterState {
     const int64_t *goff;  // per graph: first position (count + 1 entries)
     const int64_t *gdstart;  // per graph: first position of its dangling tail
     int32_t ngraph;
-    int32_t pad2_;
+    int32_t nchunk;       // batch: fixed chunks of positions for the per-graph sums
+    const int64_t *cstart;   // per chunk: first position (nchunk + 1 entries)
+    const int32_t *cgraph;   // per chunk: its graph
+    const int32_t *gchunk;   // per graph: first chunk (ngraph + 1 entries)
+    double2 *cpart;          // per chunk: (L1 change, dangling mass) of the iteration
 };
 
 }  // namespace spg
