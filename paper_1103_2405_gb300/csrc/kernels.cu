@@ -53,9 +53,6 @@ constexpr int kStagedBlock = 1024;
 // measured best for each (R-MAT 22 PageRank iteration 0.192 ms at 4 vs
 // 0.198 at 5; banded SpMV 0.230 ms at 5 vs 0.240 at 4).
 constexpr int kPersistMinBlocks = 5;
-#ifndef SPG_DEEP
-#define SPG_DEEP 0
-#endif
 __host__ __device__ constexpr int persist_minb(int mode)
 {
     return (mode == EPI_RAW || mode == EPI_RAW_PAT) ? kPersistMinBlocks : 4;
@@ -489,31 +486,6 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
                 const int64_t s = (int64_t)i * d.w + lane;
                 float acc = 0.f;
                 int st = 0;
-#if SPG_DEEP
-                if (nst >= 8) {
-                    // two batches of 4 steps in flight while a third gathers
-                    uint2 a0 = slab.ld(s), a1 = slab.ld(s + 32), a2 = slab.ld(s + 64), a3 = slab.ld(s + 96);
-                    uint2 b0 = slab.ld(s + 128), b1 = slab.ld(s + 160), b2 = slab.ld(s + 192), b3 = slab.ld(s + 224);
-                    for (st = 8; st + 4 <= nst; st += 4) {
-                        const int64_t q = s + st * 32;
-                        const uint2 c0 = slab.ld(q), c1 = slab.ld(q + 32), c2 = slab.ld(q + 64), c3 = slab.ld(q + 96);
-                        acc = slot_fma_g(a0, g, acc);
-                        acc = slot_fma_g(a1, g, acc);
-                        acc = slot_fma_g(a2, g, acc);
-                        acc = slot_fma_g(a3, g, acc);
-                        a0 = b0; a1 = b1; a2 = b2; a3 = b3;
-                        b0 = c0; b1 = c1; b2 = c2; b3 = c3;
-                    }
-                    acc = slot_fma_g(a0, g, acc);
-                    acc = slot_fma_g(a1, g, acc);
-                    acc = slot_fma_g(a2, g, acc);
-                    acc = slot_fma_g(a3, g, acc);
-                    acc = slot_fma_g(b0, g, acc);
-                    acc = slot_fma_g(b1, g, acc);
-                    acc = slot_fma_g(b2, g, acc);
-                    acc = slot_fma_g(b3, g, acc);
-                } else
-#endif
                 if (nst >= 4) {
                     uint2 a0 = slab.ld(s), a1 = slab.ld(s + 32), a2 = slab.ld(s + 64), a3 = slab.ld(s + 96);
                     for (st = 4; st + 4 <= nst; st += 4) {
@@ -577,25 +549,6 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
                     acc_b = slot_fma_g(c0, g, acc_b);
                 }
             } else {
-#if SPG_DEEP >= 2
-                if (d.w >= 16) {
-                    // the next 8 steps in flight while the current 8 gather
-                    uint2 a[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) a[u] = slab.ld(sa + (int64_t)u * 32);
-                    for (e = 8; e + 7 < d.w; e += 8) {
-                        uint2 b[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) b[u] = slab.ld(sa + (int64_t)(e + u) * 32);
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) acc_a = slot_fma_g(a[u], g, acc_a);
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) a[u] = b[u];
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) acc_a = slot_fma_g(a[u], g, acc_a);
-                }
-#endif
                 for (; e + 7 < d.w; e += 8) {
                     if (pf.ahead) pf.advance((unsigned)(((int64_t)b * d.w + (int64_t)e * 32) * Slots<is_pattern(MODE)>::kBytes), lane);
                     uint2 a[8];
