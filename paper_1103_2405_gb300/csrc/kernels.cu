@@ -981,6 +981,17 @@ bool launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
 // lane per column pair.
 
 constexpr int kSpmmU = 8;
+// Rows of a 32-row ELL block whose sums one pass keeps in registers (the
+// block is walked 32 / kSpmmRows times, its slots re-read each time).
+#ifndef SPG_SPMM_ROWS
+#define SPG_SPMM_ROWS 32
+#endif
+constexpr int kSpmmRows = SPG_SPMM_ROWS;
+// Rows whose epilogue operands are fetched together.
+#ifndef SPG_SPMM_EPI
+#define SPG_SPMM_EPI 8
+#endif
+constexpr int kSpmmEpi = SPG_SPMM_EPI;
 // Blocks of the first stage of the deterministic column sums.
 constexpr int kColsumBlocks = 152;
 constexpr size_t kSpmmTileBytes = (size_t)kWarpsPerBlock * 32 * 32 * sizeof(float2);   // 64 KB
@@ -1222,62 +1233,66 @@ __device__ __forceinline__ void spmm_block(const Workload &d, const uint2 *__res
 {
     const uint2 pad = make_uint2(0xffffffffu, 0u);
     const int hp = (d.h + 31) & ~31;
+    constexpr int RB = kSpmmRows;   // rows of the block summed per pass
     for (int b = 0; b < hp; b += 32) {
         const uint32_t my_rid = b + lane < d.h ? __ldg(rows + b + lane) : 0u;
         const uint2 *blk = slab + (int64_t)b * d.w;
+        const int nr = min(32, d.h - b);
         for (int c0 = 0; c0 < k; c0 += 64) {
             const int j0 = c0 + 2 * lane;
-            float2 acc[32];
+            for (int r0 = 0; r0 < nr; r0 += RB) {
+                float2 acc[RB];
 #pragma unroll
-            for (int t = 0; t < 32; ++t) acc[t] = make_float2(0.f, 0.f);
-            uint2 nxt = d.w > 0 ? __ldcs(blk + lane) : pad;
-            for (int e = 0; e < d.w; ++e) {
-                const uint2 ent = nxt;
-                nxt = e + 1 < d.w ? __ldcs(blk + (int64_t)(e + 1) * 32 + lane) : pad;
+                for (int t = 0; t < RB; ++t) acc[t] = make_float2(0.f, 0.f);
+                uint2 nxt = d.w > 0 ? __ldcs(blk + lane) : pad;
+                for (int e = 0; e < d.w; ++e) {
+                    const uint2 ent = nxt;
+                    nxt = e + 1 < d.w ? __ldcs(blk + (int64_t)(e + 1) * 32 + lane) : pad;
 #pragma unroll
-                for (int t0 = 0; t0 < 32; t0 += kSpmmU) {
-                    float2 p[kSpmmU];
-                    float vv[kSpmmU];
+                    for (int t0 = 0; t0 < RB; t0 += kSpmmU) {
+                        float2 p[kSpmmU];
+                        float vv[kSpmmU];
 #pragma unroll
-                    for (int u = 0; u < kSpmmU; ++u) {
-                        const int c = __shfl_sync(kFull, (int)ent.x, t0 + u);
-                        vv[u] = __shfl_sync(kFull, __uint_as_float(ent.y), t0 + u);
-                        p[u] = gather2<EVEN>(X, c, k, j0);
-                    }
+                        for (int u = 0; u < kSpmmU; ++u) {
+                            const int c = __shfl_sync(kFull, (int)ent.x, r0 + t0 + u);
+                            vv[u] = __shfl_sync(kFull, __uint_as_float(ent.y), r0 + t0 + u);
+                            p[u] = gather2<EVEN>(X, c, k, j0);
+                        }
 #pragma unroll
-                    for (int u = 0; u < kSpmmU; ++u) {
-                        acc[t0 + u].x = fmaf(vv[u], p[u].x, acc[t0 + u].x);
-                        acc[t0 + u].y = fmaf(vv[u], p[u].y, acc[t0 + u].y);
+                        for (int u = 0; u < kSpmmU; ++u) {
+                            acc[t0 + u].x = fmaf(vv[u], p[u].x, acc[t0 + u].x);
+                            acc[t0 + u].y = fmaf(vv[u], p[u].y, acc[t0 + u].y);
+                        }
                     }
                 }
-            }
-            // the epilogue reads the sums back row by row from the warp's
-            // shared-memory tile (one 64-column row per step, lane l holds
-            // columns 2l, 2l+1): a rolled loop, so the 32 sums are not live
-            // across 32 inlined epilogues
+                // the epilogue reads the sums back row by row from the warp's
+                // shared-memory tile (one 64-column row per step, lane l holds
+                // columns 2l, 2l+1): a rolled loop, so the sums are not live
+                // across inlined epilogues
 #pragma unroll
-            for (int t = 0; t < 32; ++t) tile[t * 32 + lane] = acc[t];
-            __syncwarp();
-            const int nr = min(32, d.h - b);
+                for (int t = 0; t < RB; ++t) tile[t * 32 + lane] = acc[t];
+                __syncwarp();
+                const int nrr = min(RB, nr - r0);
 #pragma unroll 1
-            for (int t0 = 0; t0 < nr; t0 += 8) {
-                uint32_t rid[8];
-                RowPreK pre[8];
+                for (int t0 = 0; t0 < nrr; t0 += kSpmmEpi) {
+                    uint32_t rid[kSpmmEpi];
+                    RowPreK pre[kSpmmEpi];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    rid[u] = __shfl_sync(kFull, my_rid, (t0 + u) & 31);
-                    pre[u] = prefetch_row_k<MODE>(rid[u], t0 + u < nr, X, Y, k, j0);
-                }
+                    for (int u = 0; u < kSpmmEpi; ++u) {
+                        rid[u] = __shfl_sync(kFull, my_rid, (r0 + t0 + u) & 31);
+                        pre[u] = prefetch_row_k<MODE>(rid[u], t0 + u < nrr, X, Y, k, j0);
+                    }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (t0 + u < nr) {
-                        const float2 a = tile[(t0 + u) * 32 + lane];
-                        spmm_finish_pre<MODE>(E, sv, rid[u], a.x, a.y, pre[u], c0, k, lane, X, Y, seeds,
-                                              delta_k, redk, acc4);
+                    for (int u = 0; u < kSpmmEpi; ++u) {
+                        if (t0 + u < nrr) {
+                            const float2 a = tile[(t0 + u) * 32 + lane];
+                            spmm_finish_pre<MODE>(E, sv, rid[u], a.x, a.y, pre[u], c0, k, lane, X, Y, seeds,
+                                                  delta_k, redk, acc4);
+                        }
                     }
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
 }
