@@ -982,16 +982,14 @@ bool launch_part(int mode, const PartView &pv, const SplitView &sv, const float 
 
 constexpr int kSpmmU = 8;
 // Rows of a 32-row ELL block whose sums one pass keeps in registers (the
-// block is walked 32 / kSpmmRows times, its slots re-read each time).
-#ifndef SPG_SPMM_ROWS
-#define SPG_SPMM_ROWS 32
-#endif
-constexpr int kSpmmRows = SPG_SPMM_ROWS;
+// block is walked 32 / rows times, its slots re-read each time) and resident
+// blocks per SM, per mode: the plain SpMM trades register rows for a third
+// block per SM (4.03 -> 3.76 ms at k = 64, R-MAT 22); the RWR epilogue needs
+// the registers (3.40 ms at 32 rows and two blocks, 5.2 ms at 16 and three).
+__host__ __device__ constexpr int spmm_rows(int mode) { return mode == EPI_RAW ? 16 : 32; }
+__host__ __device__ constexpr int spmm_minb(int mode) { return mode == EPI_RAW ? 3 : 2; }
 // Rows whose epilogue operands are fetched together.
-#ifndef SPG_SPMM_EPI
-#define SPG_SPMM_EPI 8
-#endif
-constexpr int kSpmmEpi = SPG_SPMM_EPI;
+constexpr int kSpmmEpi = 4;
 // Blocks of the first stage of the deterministic column sums.
 constexpr int kColsumBlocks = 152;
 constexpr size_t kSpmmTileBytes = (size_t)kWarpsPerBlock * 32 * 32 * sizeof(float2);   // 64 KB
@@ -1233,7 +1231,7 @@ __device__ __forceinline__ void spmm_block(const Workload &d, const uint2 *__res
 {
     const uint2 pad = make_uint2(0xffffffffu, 0u);
     const int hp = (d.h + 31) & ~31;
-    constexpr int RB = kSpmmRows;   // rows of the block summed per pass
+    constexpr int RB = spmm_rows(MODE);   // rows of the block summed per pass
     for (int b = 0; b < hp; b += 32) {
         const uint32_t my_rid = b + lane < d.h ? __ldg(rows + b + lane) : 0u;
         const uint2 *blk = slab + (int64_t)b * d.w;
@@ -1300,11 +1298,8 @@ __device__ __forceinline__ void spmm_block(const Workload &d, const uint2 *__res
 // SpMM over one part.  Split rows: chunk partials (k floats per chunk slot)
 // in sv.partial, combined in chunk order by the last chunk.  Per-block
 // column sums for RWR into redk[(slot * 2 + q) * k + j] (q = 0: L1, 1: dangling).
-#ifndef SPG_SPMM_MINB
-#define SPG_SPMM_MINB 2
-#endif
 template <int MODE, bool EVEN>
-__global__ void __launch_bounds__(kBlock, SPG_SPMM_MINB)
+__global__ void __launch_bounds__(kBlock, spmm_minb(MODE))
 k_part_spmm(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__restrict__ Yout,
             int k, const IterState *__restrict__ st, const int32_t *__restrict__ seeds,
             const double *__restrict__ delta_k, double *__restrict__ redk)
