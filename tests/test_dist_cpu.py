@@ -47,3 +47,35 @@ def test_two_rank_aggregation_takes_the_slowest_rank():
     t_max, ups = out[0]
     assert t_max == 20.0
     assert ups == pytest.approx(2 * 1000.0 / 0.020)
+
+
+def _rank_fails(rank, world, port, out):
+    import datetime
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=10))
+    import bench
+    if rank == 1:
+        out[rank] = "left"
+        os._exit(3)          # a replica that dies between steps, before the aggregation
+    try:
+        bench.aggregate_ranks(12.0, 1000.0, world)
+        out[rank] = "no error"
+    except Exception as exc:  # the surviving rank learns of it from the collective
+        out[rank] = "error: " + type(exc).__name__
+
+
+def test_a_rank_that_dies_is_detected_by_the_others():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_fails, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert procs[1].exitcode == 3 and out[1] == "left"
+    assert procs[0].exitcode == 0 and out[0].startswith("error")
