@@ -1973,51 +1973,27 @@ void launch_csr_vector(int mode, int64_t n, const int64_t *rp, const int32_t *co
 
 // ------------------------------------------------------ differentiable RWR --
 
-// Softmax of the logits over each node's out-edges, written into the packed
-// slots of the forward and transposed layouts.  A node's edges go to an
-// 8-lane segment of a warp (four nodes per warp at once): the average node
-// has a few edges, so a whole warp per node would idle most lanes and
-// serialise the loads' latency node after node.
-constexpr int kEdgeLanes = 8;
-
-__device__ __forceinline__ unsigned seg_mask(int lane)
-{
-    return ((1u << kEdgeLanes) - 1u) << (lane & ~(kEdgeLanes - 1));
-}
-
-__device__ __forceinline__ float seg_max(float v, unsigned mask)
-{
-#pragma unroll
-    for (int o = kEdgeLanes / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, kEdgeLanes));
-    return v;
-}
-
-__device__ __forceinline__ float seg_sum(float v, unsigned mask)
-{
-#pragma unroll
-    for (int o = kEdgeLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, kEdgeLanes);
-    return v;
-}
-
+// Softmax of the logits over each node's out-edges (one warp per node),
+// written into the packed slots of the forward and transposed layouts.
 __global__ void k_edge_softmax(int64_t n, const int64_t *__restrict__ rp,
                                const float *__restrict__ theta, const int64_t *__restrict__ es,
                                uint2 *slab, const int64_t *__restrict__ est, uint2 *slab_t,
                                float *__restrict__ P)
 {
-    const int sl = threadIdx.x & (kEdgeLanes - 1);
-    const unsigned mask = seg_mask(threadIdx.x & 31);
-    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kEdgeLanes; u < n;
-         u += ((int64_t)gridDim.x * blockDim.x) / kEdgeLanes) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int64_t b = rp[u], e = rp[u + 1];
         if (b == e) continue;
         float m = -INFINITY;
-        for (int64_t q = b + sl; q < e; q += kEdgeLanes) m = fmaxf(m, theta[q]);
-        m = seg_max(m, mask);
+        for (int64_t q = b + lane; q < e; q += 32) m = fmaxf(m, theta[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
         float sum = 0.f;
-        for (int64_t q = b + sl; q < e; q += kEdgeLanes) sum += __expf(theta[q] - m);
-        sum = seg_sum(sum, mask);
+        for (int64_t q = b + lane; q < e; q += 32) sum += __expf(theta[q] - m);
+        sum = warp_sum(sum);
         const float inv = 1.f / sum;
-        for (int64_t q = b + sl; q < e; q += kEdgeLanes) {
+        for (int64_t q = b + lane; q < e; q += 32) {
             const float p = __expf(theta[q] - m) * inv;
             if (P) P[q] = p;
             if (es) slab[es[q]].y = __float_as_uint(p);
@@ -2030,28 +2006,26 @@ void launch_edge_softmax(int64_t n, const int64_t *a_rp, const float *theta,
                          const int64_t *edge_slot, uint2 *slab, const int64_t *edge_slot_t,
                          uint2 *slab_t, float *P_out, cudaStream_t s)
 {
-    k_edge_softmax<<<grid_for(n * kEdgeLanes), 256, 0, s>>>(n, a_rp, theta, edge_slot, slab,
-                                                            edge_slot_t, slab_t, P_out);
+    k_edge_softmax<<<grid_for(n * 32), 256, 0, s>>>(n, a_rp, theta, edge_slot, slab, edge_slot_t,
+                                                    slab_t, P_out);
     count_launches(1);
 }
 
-// dL/dtheta over each node's out-edges (8-lane segments as above).
 __global__ void k_edge_grad(int64_t n, const int64_t *__restrict__ rp,
                             const int32_t *__restrict__ col, const float *__restrict__ P,
                             const float *__restrict__ lam, const float *__restrict__ r, float c,
                             float *__restrict__ dth)
 {
-    const int sl = threadIdx.x & (kEdgeLanes - 1);
-    const unsigned mask = seg_mask(threadIdx.x & 31);
-    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kEdgeLanes; u < n;
-         u += ((int64_t)gridDim.x * blockDim.x) / kEdgeLanes) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int64_t b = rp[u], e = rp[u + 1];
         if (b == e) continue;
         const float cr = c * r[u];
         float dot = 0.f;
-        for (int64_t q = b + sl; q < e; q += kEdgeLanes) dot = fmaf(P[q], cr * lam[col[q]], dot);
-        dot = seg_sum(dot, mask);
-        for (int64_t q = b + sl; q < e; q += kEdgeLanes) dth[q] = P[q] * (cr * lam[col[q]] - dot);
+        for (int64_t q = b + lane; q < e; q += 32) dot = fmaf(P[q], cr * lam[col[q]], dot);
+        dot = warp_sum(dot);
+        for (int64_t q = b + lane; q < e; q += 32) dth[q] = P[q] * (cr * lam[col[q]] - dot);
     }
 }
 
@@ -2059,7 +2033,7 @@ void launch_edge_grad(int64_t n, const int64_t *a_rp, const int32_t *a_col, cons
                       const float *lambda, const float *r, float c, float *dtheta,
                       cudaStream_t s)
 {
-    k_edge_grad<<<grid_for(n * kEdgeLanes), 256, 0, s>>>(n, a_rp, a_col, P, lambda, r, c, dtheta);
+    k_edge_grad<<<grid_for(n * 32), 256, 0, s>>>(n, a_rp, a_col, P, lambda, r, c, dtheta);
     count_launches(1);
 }
 
