@@ -579,6 +579,18 @@ def main():
     e2e = {"value": 2.0 * nnz * args.steps / e2e_s / 1e9, "unit": "GFLOP/s",
            "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n}
 
+    # ---- reduced-byte variant beside it: pattern-only slots (4 B per entry,
+    # 1/outdeg folded into the gathered vector), same iteration
+    fp = spg.Format(rp, col, kind="pagerank", pattern_only=True)
+    fp.pagerank(DAMPING, tol=0.0, max_iter=3, like=like)
+    pat_ms = float(fp.time_parts(mode=1, reps=max(20, args.steps // 2)).sum())
+    pat_bytes = 4 * nnz + 4 * n + 4 * n + 4 * n + 4 * n + 4 * n + 4 * n   # + z write, inv_deg read
+    pattern_only = {"kernel_ms": pat_ms,
+                    "effective_gbs": alg_bytes / (pat_ms * 1e-3) / 1e9,
+                    "hbm_gbs_own_bytes": pat_bytes / (pat_ms * 1e-3) / 1e9,
+                    "note": "effective = the full format's algorithmic bytes over this kernel's time"}
+    del fp
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_leg(rp, col, nnz)
@@ -601,6 +613,7 @@ def main():
             "spmv_gflops_public_call": 2.0 * nnz / (spmv_ms * 1e-3) / 1e9,
             "spmv_kernel_ms": float(raw_ms.sum()),
             "baselines_same_gpu": base,
+            "pattern_only_variant": pattern_only,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
