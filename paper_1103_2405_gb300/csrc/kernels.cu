@@ -53,12 +53,6 @@ constexpr int kStagedBlock = 1024;
 // measured best for each (R-MAT 22 PageRank iteration 0.192 ms at 4 vs
 // 0.198 at 5; banded SpMV 0.230 ms at 5 vs 0.240 at 4).
 constexpr int kPersistMinBlocks = 5;
-#ifndef SPG_SLOT_L1NA
-#define SPG_SLOT_L1NA 0
-#endif
-#ifndef SPG_X_L1LAST
-#define SPG_X_L1LAST 0
-#endif
 __host__ __device__ constexpr int persist_minb(int mode)
 {
     return (mode == EPI_RAW || mode == EPI_RAW_PAT) ? kPersistMinBlocks : 4;
@@ -401,16 +395,7 @@ __device__ __forceinline__ void fused_check(const FuseCheck &fc, const double2 *
 // ones: columns are in decreasing-length order) with global fallback.
 struct GatherGlobal {
     const float *__restrict__ x;
-    __device__ __forceinline__ float operator()(int c) const
-    {
-#if SPG_X_L1LAST
-        float v;
-        asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(x + c));
-        return v;
-#else
-        return __ldg(x + c);
-#endif
-    }
+    __device__ __forceinline__ float operator()(int c) const { return __ldg(x + c); }
 };
 struct GatherStaged {
     const float *__restrict__ x;
@@ -462,40 +447,18 @@ struct SlabPrefetch {
 __host__ __device__ constexpr bool is_pattern(int mode) { return mode == EPI_PR_PAT || mode == EPI_RAW_PAT; }
 
 template <bool PAT> struct Slots;
-// Slot loads bypass L1 (read once; L1 is left to the x gathers).
-__device__ __forceinline__ uint2 ld_slot_na(const uint2 *a)
-{
-#if SPG_SLOT_L1NA
-    uint2 v;
-    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(a));
-    return v;
-#else
-    return __ldcs(a);
-#endif
-}
-__device__ __forceinline__ uint32_t ld_slot_na(const uint32_t *a)
-{
-#if SPG_SLOT_L1NA
-    uint32_t v;
-    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(a));
-    return v;
-#else
-    return __ldcs(a);
-#endif
-}
-
 template <> struct Slots<false> {
     static constexpr int kBytes = 8;
     const uint2 *__restrict__ p;
     __device__ __forceinline__ Slots(const PartView &pv, int64_t off) : p(pv.slab + off) {}
-    __device__ __forceinline__ uint2 ld(int64_t i) const { return ld_slot_na(p + i); }
+    __device__ __forceinline__ uint2 ld(int64_t i) const { return __ldcs(p + i); }
     __device__ __forceinline__ const char *bytes_at(int64_t i) const { return reinterpret_cast<const char *>(p + i); }
 };
 template <> struct Slots<true> {
     static constexpr int kBytes = 4;
     const uint32_t *__restrict__ p;
     __device__ __forceinline__ Slots(const PartView &pv, int64_t off) : p(pv.slab4 + off) {}
-    __device__ __forceinline__ uint2 ld(int64_t i) const { return make_uint2(ld_slot_na(p + i), 0x3f800000u); }
+    __device__ __forceinline__ uint2 ld(int64_t i) const { return make_uint2(__ldcs(p + i), 0x3f800000u); }
     __device__ __forceinline__ const char *bytes_at(int64_t i) const { return reinterpret_cast<const char *>(p + i); }
 };
 
