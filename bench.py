@@ -591,6 +591,22 @@ def main():
                     "note": "effective = the full format's algorithmic bytes over this kernel's time"}
     del fp
 
+    # ---- storage-rule ablation (the composite format's special cases):
+    # every workload CSR-vector (rule 2), every workload ELL (rule 3), the
+    # paper's w >= h rule (0), against the default (1); model prediction
+    # beside the measured kernel time.  Skipped above 8M nodes (build time).
+    ablation = None
+    if n <= (1 << 23):
+        ablation = {"default_rule1": {"kernel_ms": k_ms, "predicted_ms": info["predicted_ms"],
+                                      "padded_slots": info["padded_slots"]}}
+        for rule, name in ((0, "paper_rule0"), (2, "all_csr_vector_rule2"), (3, "all_ell_rule3")):
+            fa = spg.Format(rp, col, kind="pagerank", layout_rule=rule)
+            fa.pagerank(DAMPING, tol=0.0, max_iter=3, like=like)
+            ia = fa.info()
+            ablation[name] = {"kernel_ms": float(fa.time_parts(mode=1, reps=20).sum()),
+                              "predicted_ms": ia["predicted_ms"], "padded_slots": ia["padded_slots"]}
+            del fa
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_leg(rp, col, nnz)
@@ -614,6 +630,7 @@ def main():
             "spmv_kernel_ms": float(raw_ms.sum()),
             "baselines_same_gpu": base,
             "pattern_only_variant": pattern_only,
+            "storage_rule_ablation": ablation,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

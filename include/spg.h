@@ -97,7 +97,9 @@ typedef struct {
      * tuned by the performance model, 0 = never split, > 0 = fixed. */
     int64_t heavy_row;
     /* Storage rule of a workload: 0 = the paper's (row-major iff w >= h),
-     * 1 = the major with fewer padded slots (row-major on a tie).  Default 1. */
+     * 1 = the major with fewer padded slots (row-major on a tie; default),
+     * 2 = every workload row-major (the CSR-vector special case), 3 = every
+     * workload column-major (the ELL special case; Section 5). */
     int layout_rule;
     /* Maximum resident warps of the whole GPU used by Algorithms 2-3.
      * 0 = query the current device (SMs x resident warps of the kernel). */

@@ -131,6 +131,8 @@ static inline int64_t ru32(int64_t v) { return (v + 31) / 32 * 32; }
 static inline int pick_major(int rule, int64_t w, int64_t h)
 {
     if (rule == 0) return w >= h ? 0 : 1;                 // the paper's rule
+    if (rule == 2) return 0;                              // every workload CSR-vector
+    if (rule == 3) return 1;                              // every workload ELL
     return h * ru32(w) <= ru32(h) * w ? 0 : 1;            // fewer padded slots
 }
 

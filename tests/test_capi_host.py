@@ -61,6 +61,8 @@ CASES = [  # (scale, ef, tile_width, heavy, rule, max_warps, max_rows)
     (10, 16, 128, -1, 0, 13, -1),
     (12, 8, -1, -1, 1, 9728, 256),
     (12, 8, 512, -1, 1, 40, 37),
+    (12, 8, 1024, -1, 2, 300, -1),
+    (12, 8, -1, 64, 3, 9728, -1),
 ]
 
 

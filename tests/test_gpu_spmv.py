@@ -72,6 +72,8 @@ CONFIGS = [
     ("rmat14", dict(tile_width=2048)),                         # dense tiles + sparse tail
     ("rmat14", dict(tile_width=256, heavy_row=0)),             # no split rows
     ("rmat14", dict(tile_width=4096, heavy_row=32, layout_rule=0)),
+    ("rmat14", dict(tile_width=2048, layout_rule=2)),           # all CSR-vector
+    ("rmat14", dict(layout_rule=3)),                            # all ELL
     ("rmat12", dict(tile_width=100, wl=96)),                   # ragged tile width, fixed WL
     ("hub", dict()),                                           # split hub row
     ("hub", dict(heavy_row=0)),                                # one warp for the hub row

@@ -180,3 +180,19 @@ def test_plan_format_small_rmat():
             total[r] += L
     assert np.array_equal(total, indeg[plan["inv"]])
     assert np.array_equal(np.sort(plan["zero_rows"]), np.flatnonzero(indeg[plan["inv"]] == 0))
+
+
+@pytest.mark.parametrize("rule,major", [(2, 0), (3, 1)])
+def test_forced_storage_rules_are_the_special_cases(rule, major):
+    # rule 2: every workload row-major (CSR-vector); rule 3: every workload
+    # column-major (ELL); the ranking and the rectangles do not depend on
+    # the rule, only the storage major (and so the padded size) does
+    rng = np.random.default_rng(11)
+    n = 400
+    rl = rng.zipf(1.7, n).clip(0, 2000).astype(np.int64)
+    ids = rng.permutation(n).astype(np.int64)
+    base = oracle.partition_tile(ids, rl, heavy=0, wl=96, max_warps=29, rule=1, table=_const_table())
+    part = oracle.partition_tile(ids, rl, heavy=0, wl=96, max_warps=29, rule=rule, table=_const_table())
+    assert np.all(np.asarray(part["wl_major"]) == major)
+    for k in ("rank_row", "rank_len", "wl_first", "wl_h", "wl_w"):
+        assert np.array_equal(np.asarray(part[k]), np.asarray(base[k]))
