@@ -117,6 +117,8 @@ struct spg_format_t {
     int64_t *d_arp = nullptr;
     int32_t *d_acol = nullptr;
     float *d_P = nullptr;
+    int32_t *d_heavy = nullptr;      // nodes of many out-edges (block-per-node edge kernels)
+    int nheavy = 0;
     // workspace
     DevBuf<float> x, y, stage_in, stage_out;
     DevBuf<double2> red;
@@ -180,6 +182,7 @@ struct spg_format_t {
         if (bwd) bwd->free_device();
         cudaFree(d_rp); cudaFree(d_col); cudaFree(d_val); cudaFree(d_dangling);
         cudaFree(d_row_half); cudaFree(d_arp); cudaFree(d_acol); cudaFree(d_P); cudaFree(d_owner);
+        cudaFree(d_heavy);
         red_ranks.release(); rank_states.release();
         cudaFree(d_goff); cudaFree(d_gdstart); cudaFree(d_gid); cudaFree(d_giters);
         cudaFree(d_status);
@@ -504,6 +507,11 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
             if (kind == SPG_KIND_WEIGHTED) {
                 CK(upload(&h->d_arp, rp, (size_t)n + 1));
                 CK(upload(&h->d_acol, col, (size_t)nnz));
+                std::vector<int32_t> heavy;
+                for (int64_t v = 0; v < n; ++v)
+                    if (rp[v + 1] - rp[v] > edge_heavy_degree()) heavy.push_back((int32_t)v);
+                h->nheavy = (int)heavy.size();
+                CK(upload(&h->d_heavy, heavy.data(), heavy.size()));
                 CK(upload(&h->d_P, mval.data(), (size_t)nnz));
                 if (o.build_transpose) {
                     // M^T: rows u (sources), entries (v, P_e) -> column source of M^T is
@@ -1483,7 +1491,8 @@ extern "C" spg_status spg_set_edge_logits(spg_handle h, const float *theta, void
     }
     Layout *b = h->bwd.get();
     launch_edge_softmax(h->n_graph, h->d_arp, td, h->fwd.d_edge_slot, h->fwd.d_slab,
-                        b ? b->d_edge_slot : nullptr, b ? b->d_slab : nullptr, h->d_P, s);
+                        b ? b->d_edge_slot : nullptr, b ? b->d_slab : nullptr, h->d_P, h->d_heavy,
+                        h->nheavy, s);
     CK(cudaGetLastError());
     return SPG_OK;
 }
@@ -1545,7 +1554,8 @@ extern "C" spg_status spg_rwr_adjoint(spg_handle h, float restart, int32_t seed,
         const bool dt_host = !is_device_ptr(dtheta);
         float *dt_d = dtheta;
         if (dt_host) { CK(h->stage_in.ensure((size_t)std::max(n, h->nnz_in))); dt_d = h->stage_in.p; }
-        launch_edge_grad(n, h->d_arp, h->d_acol, h->d_P, lam_d, rd, (float)c, dt_d, s);
+        launch_edge_grad(n, h->d_arp, h->d_acol, h->d_P, lam_d, rd, (float)c, dt_d, h->d_heavy,
+                         h->nheavy, s);
         if (dt_host) CK(cudaMemcpyAsync(dtheta, dt_d, h->nnz_in * sizeof(float), cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));

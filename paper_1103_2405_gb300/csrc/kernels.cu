@@ -1973,68 +1973,174 @@ void launch_csr_vector(int mode, int64_t n, const int64_t *rp, const int32_t *co
 
 // ------------------------------------------------------ differentiable RWR --
 
-// Softmax of the logits over each node's out-edges (one warp per node),
-// written into the packed slots of the forward and transposed layouts.
+// Softmax of the logits over each node's out-edges, written into the packed
+// slots of the forward and transposed layouts.  Nodes of at most
+// kEdgeHeavy out-edges take an 8-lane segment of a warp (four nodes per warp
+// at once: the typical node has a few edges, so a whole warp per node would
+// serialise the loads' latency node after node); the heavier ones (a short
+// list built with the format) take a 256-thread block each, so that a hub's
+// edges are not a long serial loop either.
+constexpr int kEdgeLanes = 8;
+constexpr int kEdgeHeavy = 64;
+
+__device__ __forceinline__ unsigned seg_mask(int lane)
+{
+    return ((1u << kEdgeLanes) - 1u) << (lane & ~(kEdgeLanes - 1));
+}
+
+__device__ __forceinline__ float seg_max(float v, unsigned mask)
+{
+#pragma unroll
+    for (int o = kEdgeLanes / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, kEdgeLanes));
+    return v;
+}
+
+__device__ __forceinline__ float seg_sum(float v, unsigned mask)
+{
+#pragma unroll
+    for (int o = kEdgeLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, kEdgeLanes);
+    return v;
+}
+
+// Block-wide max / sum of one value per thread (256 threads), result in
+// every thread.
+__device__ __forceinline__ float block_max256(float v, float *sm)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = sm[0];
+    for (int w = 1; w < 8; ++w) r = fmaxf(r, sm[w]);
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ float block_sum256(float v, float *sm)
+{
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = 0.f;
+    for (int w = 0; w < 8; ++w) r += sm[w];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void store_weight(int64_t q, float p, const int64_t *es, uint2 *slab,
+                                             const int64_t *est, uint2 *slab_t, float *P)
+{
+    if (P) P[q] = p;
+    if (es) slab[es[q]].y = __float_as_uint(p);
+    if (est) slab_t[est[q]].y = __float_as_uint(p);
+}
+
 __global__ void k_edge_softmax(int64_t n, const int64_t *__restrict__ rp,
                                const float *__restrict__ theta, const int64_t *__restrict__ es,
                                uint2 *slab, const int64_t *__restrict__ est, uint2 *slab_t,
                                float *__restrict__ P)
 {
-    const int lane = threadIdx.x & 31;
-    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n;
-         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int sl = threadIdx.x & (kEdgeLanes - 1);
+    const unsigned mask = seg_mask(threadIdx.x & 31);
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kEdgeLanes; u < n;
+         u += ((int64_t)gridDim.x * blockDim.x) / kEdgeLanes) {
         const int64_t b = rp[u], e = rp[u + 1];
-        if (b == e) continue;
+        if (b == e || e - b > kEdgeHeavy) continue;
         float m = -INFINITY;
-        for (int64_t q = b + lane; q < e; q += 32) m = fmaxf(m, theta[q]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+        for (int64_t q = b + sl; q < e; q += kEdgeLanes) m = fmaxf(m, theta[q]);
+        m = seg_max(m, mask);
         float sum = 0.f;
-        for (int64_t q = b + lane; q < e; q += 32) sum += __expf(theta[q] - m);
-        sum = warp_sum(sum);
+        for (int64_t q = b + sl; q < e; q += kEdgeLanes) sum += __expf(theta[q] - m);
+        sum = seg_sum(sum, mask);
         const float inv = 1.f / sum;
-        for (int64_t q = b + lane; q < e; q += 32) {
-            const float p = __expf(theta[q] - m) * inv;
-            if (P) P[q] = p;
-            if (es) slab[es[q]].y = __float_as_uint(p);
-            if (est) slab_t[est[q]].y = __float_as_uint(p);
-        }
+        for (int64_t q = b + sl; q < e; q += kEdgeLanes)
+            store_weight(q, __expf(theta[q] - m) * inv, es, slab, est, slab_t, P);
     }
+}
+
+__global__ void __launch_bounds__(256)
+k_edge_softmax_heavy(const int32_t *__restrict__ heavy, const int64_t *__restrict__ rp,
+                     const float *__restrict__ theta, const int64_t *__restrict__ es, uint2 *slab,
+                     const int64_t *__restrict__ est, uint2 *slab_t, float *__restrict__ P)
+{
+    __shared__ float sm[8];
+    const int64_t u = heavy[blockIdx.x];
+    const int64_t b = rp[u], e = rp[u + 1];
+    float m = -INFINITY;
+    for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x) m = fmaxf(m, theta[q]);
+    m = block_max256(m, sm);
+    float sum = 0.f;
+    for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x) sum += __expf(theta[q] - m);
+    sum = block_sum256(sum, sm);
+    const float inv = 1.f / sum;
+    for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x)
+        store_weight(q, __expf(theta[q] - m) * inv, es, slab, est, slab_t, P);
 }
 
 void launch_edge_softmax(int64_t n, const int64_t *a_rp, const float *theta,
                          const int64_t *edge_slot, uint2 *slab, const int64_t *edge_slot_t,
-                         uint2 *slab_t, float *P_out, cudaStream_t s)
+                         uint2 *slab_t, float *P_out, const int32_t *heavy, int nheavy,
+                         cudaStream_t s)
 {
-    k_edge_softmax<<<grid_for(n * 32), 256, 0, s>>>(n, a_rp, theta, edge_slot, slab, edge_slot_t,
-                                                    slab_t, P_out);
+    k_edge_softmax<<<grid_for(n * kEdgeLanes), 256, 0, s>>>(n, a_rp, theta, edge_slot, slab,
+                                                            edge_slot_t, slab_t, P_out);
     count_launches(1);
+    if (nheavy > 0) {
+        k_edge_softmax_heavy<<<nheavy, 256, 0, s>>>(heavy, a_rp, theta, edge_slot, slab,
+                                                    edge_slot_t, slab_t, P_out);
+        count_launches(1);
+    }
 }
 
+// dL/dtheta over each node's out-edges (segments and heavy blocks as for
+// the softmax).
 __global__ void k_edge_grad(int64_t n, const int64_t *__restrict__ rp,
                             const int32_t *__restrict__ col, const float *__restrict__ P,
                             const float *__restrict__ lam, const float *__restrict__ r, float c,
                             float *__restrict__ dth)
 {
-    const int lane = threadIdx.x & 31;
-    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n;
-         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int sl = threadIdx.x & (kEdgeLanes - 1);
+    const unsigned mask = seg_mask(threadIdx.x & 31);
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kEdgeLanes; u < n;
+         u += ((int64_t)gridDim.x * blockDim.x) / kEdgeLanes) {
         const int64_t b = rp[u], e = rp[u + 1];
-        if (b == e) continue;
+        if (b == e || e - b > kEdgeHeavy) continue;
         const float cr = c * r[u];
         float dot = 0.f;
-        for (int64_t q = b + lane; q < e; q += 32) dot = fmaf(P[q], cr * lam[col[q]], dot);
-        dot = warp_sum(dot);
-        for (int64_t q = b + lane; q < e; q += 32) dth[q] = P[q] * (cr * lam[col[q]] - dot);
+        for (int64_t q = b + sl; q < e; q += kEdgeLanes) dot = fmaf(P[q], cr * lam[col[q]], dot);
+        dot = seg_sum(dot, mask);
+        for (int64_t q = b + sl; q < e; q += kEdgeLanes) dth[q] = P[q] * (cr * lam[col[q]] - dot);
     }
+}
+
+__global__ void __launch_bounds__(256)
+k_edge_grad_heavy(const int32_t *__restrict__ heavy, const int64_t *__restrict__ rp,
+                  const int32_t *__restrict__ col, const float *__restrict__ P,
+                  const float *__restrict__ lam, const float *__restrict__ r, float c,
+                  float *__restrict__ dth)
+{
+    __shared__ float sm[8];
+    const int64_t u = heavy[blockIdx.x];
+    const int64_t b = rp[u], e = rp[u + 1];
+    const float cr = c * r[u];
+    float dot = 0.f;
+    for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x) dot = fmaf(P[q], cr * lam[col[q]], dot);
+    dot = block_sum256(dot, sm);
+    for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x) dth[q] = P[q] * (cr * lam[col[q]] - dot);
 }
 
 void launch_edge_grad(int64_t n, const int64_t *a_rp, const int32_t *a_col, const float *P,
                       const float *lambda, const float *r, float c, float *dtheta,
-                      cudaStream_t s)
+                      const int32_t *heavy, int nheavy, cudaStream_t s)
 {
-    k_edge_grad<<<grid_for(n * 32), 256, 0, s>>>(n, a_rp, a_col, P, lambda, r, c, dtheta);
+    k_edge_grad<<<grid_for(n * kEdgeLanes), 256, 0, s>>>(n, a_rp, a_col, P, lambda, r, c, dtheta);
     count_launches(1);
+    if (nheavy > 0) {
+        k_edge_grad_heavy<<<nheavy, 256, 0, s>>>(heavy, a_rp, a_col, P, lambda, r, c, dtheta);
+        count_launches(1);
+    }
 }
+
+int edge_heavy_degree() { return kEdgeHeavy; }
 
 }  // namespace spg

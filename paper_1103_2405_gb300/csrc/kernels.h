@@ -104,13 +104,17 @@ int csr_vector_blocks(int64_t n);
 
 // Edge weights: P_e = softmax over out-edges of theta, written to the slab
 // slots edge_slot[e] (forward) and edge_slot_t[e] (transposed, nullable).
+// heavy: the nheavy nodes of more than edge_heavy_degree() out-edges (one
+// block each); the others take 8-lane segments.
 void launch_edge_softmax(int64_t n, const int64_t *a_rp, const float *theta,
                          const int64_t *edge_slot, uint2 *slab, const int64_t *edge_slot_t,
-                         uint2 *slab_t, float *P_out, cudaStream_t s);
+                         uint2 *slab_t, float *P_out, const int32_t *heavy, int nheavy,
+                         cudaStream_t s);
+int edge_heavy_degree();
 // dtheta_e = P_e (G_e - sum_{e' in out(u)} P_e' G_e'), G_e = c lambda_v r_u.
 void launch_edge_grad(int64_t n, const int64_t *a_rp, const int32_t *a_col, const float *P,
                       const float *lambda, const float *r, float c, float *dtheta,
-                      cudaStream_t s);
+                      const int32_t *heavy, int nheavy, cudaStream_t s);
 
 // Resident blocks per SM of the tiled-composite SpMV kernel on this device.
 // Resident blocks per SM of the persistent plain SpMV kernel (kernel option 4).
