@@ -282,7 +282,8 @@ spg_status spg_spmv_permuted(spg_handle h, const float *x_perm, float *y_perm, v
 
 /* Y = alpha * M X + beta * Y for k vectors: X (n x k) and Y (n x k) FP32,
  * row-major with leading dimensions ldx, ldy >= k, original row order.
- * One warp per row, each lane two of the k columns.  k in [1, 1024]. */
+ * One warp per workload, each lane two of every 64-column chunk; device
+ * pointers only.  k in [1, 1024]. */
 spg_status spg_spmm(spg_handle h, const float *X, int64_t ldx, float *Y, int64_t ldy, int k,
                     float alpha, float beta, void *stream);
 
@@ -382,8 +383,10 @@ spg_status spg_batch_offsets(spg_handle h, int64_t *offsets);
 
 /* PageRank (Eq. 6, uniform dangling redistribution per graph) on every graph
  * of a batch handle at once: per iteration one tiled-composite launch over
- * all graphs, one block per graph for its L1 change and dangling mass, one
- * check block; the whole solve is one CUDA graph with a WHILE node.  Each
+ * all graphs, one block per fixed chunk of at most 8192 positions for the
+ * per-graph L1 change and dangling mass, one check block that adds each
+ * graph's chunks in order; the whole solve is one CUDA graph with a WHILE
+ * node.  Each
  * graph records the iteration at which its L1 change first went below tol;
  * the loop ends when all have (or at max_iter).  p_out: the concatenated
  * vectors, original node order within each graph.  info (nullable): count
