@@ -470,6 +470,23 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
                                             double2 *red, int lane, FSum &r0, FSum &r1)
 {
     const uint32_t *__restrict__ rows = pv.rows + d.rows;
+    if (d.w == 0) {
+        // rows without entries (the epilogue alone): kZeroBatch rows per lane
+        // per pass, their operand loads all in flight together
+        constexpr int kZeroBatch = 4;
+        for (int i0 = 0; i0 < d.h; i0 += 32 * kZeroBatch) {
+            RowPre p[kZeroBatch];
+#pragma unroll
+            for (int u = 0; u < kZeroBatch; ++u) {
+                const int i = i0 + u * 32 + lane;
+                p[u] = prefetch_row<MODE>(E, rows, i, i < d.h, x, y);
+            }
+#pragma unroll
+            for (int u = 0; u < kZeroBatch; ++u)
+                if (i0 + u * 32 + lane < d.h) finish_row_pre<MODE>(E, sv, red, p[u], 0.f, x, y, r0, r1);
+        }
+        return;
+    }
     const Slots<is_pattern(MODE)> slab{pv, d.slab};
     const int hp = d.major == 0 ? d.h : (d.h + 31) & ~31;
     SlabPrefetch pf{slab.bytes_at(0), (unsigned)((int64_t)hp * d.w * Slots<is_pattern(MODE)>::kBytes),
