@@ -87,8 +87,8 @@ typedef struct {
 typedef struct {
     /* Column tile width (Section 3.1, Solution 1; Algorithm 1).  0 = auto:
      * the largest power of two whose x slice (tile_width * 4 bytes) fits in
-     * 40 % of the L2; < 0 = no dense tiles (the whole matrix is one
-     * composite tile). */
+     * 60 % of the L2 (16M columns on GB300); < 0 = no dense tiles (the whole
+     * matrix is one composite tile). */
     int64_t tile_width;
     /* Workload size per warp (Solution 3).  0 = Algorithm 2. */
     int64_t wl;
