@@ -1,0 +1,69 @@
+"""Full-size parity on the billion-edge workload: R-MAT scale 26 (67,108,864
+nodes, edge factor 16, 1,060,377,406 edges after dedup), default build options
+(the launch configuration bench.py times).  The oracle cannot run a whole
+PageRank at this size in test time, so: SpMV on sampled rows (random ones
+plus the heaviest, split rows) against the oracle row by row; one fused
+PageRank iteration checked on sampled rows against Eq. 6 applied by the
+oracle to the GPU's previous iterate; and the solve to L1 tol 1e-7 checked by
+its invariants (sum 1, final L1 change below tol)."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+import oracle
+import paper_1103_2405_gb300 as spg
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+C = 0.85
+
+
+@pytest.fixture(scope="module")
+def g26():
+    rp, col = graphgen.rmat(26, 16, seed=1)
+    M = oracle.build_M(rp, col)
+    f = spg.Format(rp, col, kind="pagerank")
+    return rp, col, M, f
+
+
+def _rows(M, n):
+    indeg = np.diff(M[0])
+    heavy = np.argpartition(-indeg, 256)[:256]
+    rng = np.random.default_rng(1)
+    return np.unique(np.concatenate([heavy, rng.integers(0, n, 8192), [0, n - 1]]))
+
+
+def test_spmv_sampled_rows_scale26(g26):
+    rp, col, M, f = g26
+    n = rp.shape[0] - 1
+    assert f.info()["ntile"] >= 1 and f.info()["split_rows"] > 0
+    x = graphgen.uniform(n, 2)
+    y = f.spmv(torch.from_numpy(x).to(DEV))
+    torch.cuda.synchronize()
+    y = y.cpu().numpy()
+    rows = _rows(M, n)
+    ref = oracle.spmv_rows(M, rows, x)
+    bound = oracle.spmv_rows((M[0], M[1], np.abs(M[2])), rows, x)
+    assert np.all(np.abs(y[rows] - ref) <= 1e-5 * bound + 1e-30)
+    assert np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+def test_pagerank_step_and_solve_scale26(g26):
+    rp, col, M, f = g26
+    n = rp.shape[0] - 1
+    like = torch.empty(0, device=DEV)
+    p19, _ = f.pagerank(C, tol=0.0, max_iter=19, like=like)
+    p20, _ = f.pagerank(C, tol=0.0, max_iter=20, like=like)
+    p19 = p19.cpu().numpy().astype(np.float64)
+    p20 = p20.cpu().numpy()
+    dangling = np.diff(rp) == 0
+    delta = p19[dangling].sum()
+    rows = _rows(M, n)
+    ref = C * oracle.spmv_rows(M, rows, p19) + (C * delta + 1.0 - C) / n
+    bound = C * oracle.spmv_rows((M[0], M[1], np.abs(M[2])), rows, p19) + (C * delta + 1.0 - C) / n
+    assert np.all(np.abs(p20[rows] - ref) <= 2e-5 * bound)
+    assert abs(p20.astype(np.float64).sum() - 1.0) <= 1e-5
+    p, info = f.pagerank(C, tol=1e-7, max_iter=1000, like=like)
+    assert info["last_l1"] < 1e-7 and info["iters"] < 200
+    assert abs(p.double().sum().item() - 1.0) <= 1e-5
