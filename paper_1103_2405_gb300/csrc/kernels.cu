@@ -35,9 +35,9 @@ static inline int grid_for(int64_t n, int per = 256)
     if (g > 152 * 64) g = 152 * 64;
     return (int)(g > 0 ? g : 1);
 }
-// Resident blocks per SM the SpMV kernel is compiled for (8 x 8 warps = the
-// SM's 64-warp limit): the gather is latency bound, so occupancy is what
-// keeps enough loads in flight.
+// Resident blocks per SM of the plain one-warp-per-workload kernel (option
+// 2): the gather is latency bound, so occupancy is what keeps enough loads
+// in flight.
 #ifndef SPG_PART_MINB
 #define SPG_PART_MINB 6
 #endif
@@ -624,15 +624,19 @@ k_part(PartView pv, SplitView sv, const float *__restrict__ xin, float *__restri
         block_reduce_store<MODE>(r0, r1, red + pv.red_base + blockIdx.x);
 }
 
-// Same computation with the part's densest x columns staged in shared
-// memory: one persistent 32-warp block per SM copies x[c0, c0 + S) into
-// shared memory (the GB300 counterpart of the paper's texture-cache tile,
-// Section 3.1 Solution 1), then its warps take workloads in order from a
-// counter (pv.sched[0]) in claim units -- runs of consecutive workloads
-// grouped by the builder so that small workloads are claimed several at a
-// time (one atomic on one address per claim bounds the claim rate) while
-// large ones stay alone; the last warp out resets the counters for the next
-// launch (pv.sched[1] counts finished warps).  No waits between blocks.
+// The persistent form of the same computation, two instantiations:
+// * NT = 256 (the default kernel): MINB 8-warp blocks per SM, x gathered
+//   through L1/L2;
+// * NT = 1024 (option 1): one 32-warp block per SM that first copies the
+//   part's densest columns x[c0, c0 + S) into shared memory (the GB300
+//   counterpart of the paper's texture-cache tile, Section 3.1 Solution 1).
+// Warps take workloads in order from a counter (pv.sched[0]) in claim units
+// -- runs of consecutive workloads grouped by the builder so that small
+// workloads are claimed several at a time (one atomic on one address per
+// claim bounds the claim rate) while large ones stay alone; the last warp
+// out resets the counters for the next launch (pv.sched[1] counts finished
+// warps).  No block waits on another; the fused check (fc.nred > 0) runs in
+// whichever block finishes last.
 template <int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
