@@ -150,6 +150,10 @@ struct spg_format_t {
     int kernel = 4;              // 1: staged x slice, 2: plain, 3: TMA ring, 4 (and 0): persistent plain
     int persist_blocks = 5;      // kernel 4: resident 8-warp blocks per SM
     uint32_t *d_status = nullptr;   // set by kernels whose bounded waits ran out
+    // pinned host copies the loop's final state and the status word are read
+    // back into without a synchronisation of their own
+    IterState *hs_pinned = nullptr;
+    uint32_t *status_pinned = nullptr;
     int loop_mode = 0;           // 0: CUDA-graph WHILE loop, 1: host loop
     bool separate_check = false; // convergence check in its own kernel (not fused)
     int num_sms = 152;
@@ -190,6 +194,8 @@ struct spg_format_t {
         red_ranks.release(); rank_states.release();
         cudaFree(d_goff); cudaFree(d_gdstart); cudaFree(d_gid); cudaFree(d_giters);
         cudaFree(d_status);
+        if (hs_pinned) cudaFreeHost(hs_pinned);
+        if (status_pinned) cudaFreeHost(status_pinned);
         cudaFree(d_gbase); cudaFree(d_gl1); cudaFree(d_gdelta);
         cudaFree(d_cstart); cudaFree(d_cgraph); cudaFree(d_gchunk); cudaFree(d_cpart);
         x.release(); y.release(); stage_in.release(); stage_out.release(); red.release();
@@ -340,6 +346,9 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     }
     CK(cudaMalloc((void **)&h->d_status, sizeof(uint32_t)));
     CK(cudaMemset(h->d_status, 0, sizeof(uint32_t)));
+    CK(cudaMallocHost((void **)&h->hs_pinned, sizeof(IterState)));
+    CK(cudaMallocHost((void **)&h->status_pinned, sizeof(uint32_t)));
+    *h->status_pinned = 0u;
     CK(h->rt_fwd.sched.ensure(2 * h->fwd.parts.size() + 1));
     CK(cudaMemset(h->rt_fwd.sched.p, 0, (2 * h->fwd.parts.size() + 1) * sizeof(uint32_t)));
     CK(cudaMalloc((void **)&h->d_state, sizeof(IterState)));
@@ -984,8 +993,20 @@ static spg_status take_status(spg_handle h)
     return fail(SPG_ERR_TIMEOUT, "a bounded wait on a TMA copy ran out in the SpMV kernel");
 }
 
-static spg_status run_loop(spg_handle h, LoopGraph *g, int max_iter, IterState *hs,
-                           spg_iter_info *info, cudaStream_t s)
+// Upload the iteration state through the handle's pinned copy (an
+// asynchronous copy from pageable memory would stage synchronously).  The
+// pinned copy is next written by the loop's read-back, later in stream order.
+static spg_status upload_state(spg_handle h, const IterState &hs, cudaStream_t s)
+{
+    *h->hs_pinned = hs;
+    CK(cudaMemcpyAsync(h->d_state, h->hs_pinned, sizeof(IterState), cudaMemcpyHostToDevice, s));
+    return SPG_OK;
+}
+
+// Enqueue the loop `g` (max_iter > 0) and the read-back of the final state
+// and the status word into pinned host memory; no synchronisation, so the
+// caller can queue its output passes behind it and synchronise once.
+static spg_status launch_loop(spg_handle h, LoopGraph *g, int max_iter, cudaStream_t s)
 {
     if (max_iter > 0) {
         CK(cudaEventRecord(h->ev0, s));
@@ -1005,10 +1026,22 @@ static spg_status run_loop(spg_handle h, LoopGraph *g, int max_iter, IterState *
         }
         CK(cudaEventRecord(h->ev1, s));
     }
-    CK(cudaMemcpyAsync(hs, h->d_state, sizeof(IterState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    spg_status stw = take_status(h);
-    if (stw != SPG_OK) return stw;
+    CK(cudaMemcpyAsync(h->hs_pinned, h->d_state, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->status_pinned, h->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    return SPG_OK;
+}
+
+// After the stream has synchronised: the final state, the status word, the
+// launch count and the info record of a launch_loop.
+static spg_status finish_loop(spg_handle h, LoopGraph *g, int max_iter, IterState *hs,
+                              spg_iter_info *info)
+{
+    *hs = *h->hs_pinned;
+    if (*h->status_pinned) {
+        *h->status_pinned = 0u;
+        CK(cudaMemset(h->d_status, 0, sizeof(uint32_t)));
+        return fail(SPG_ERR_TIMEOUT, "a bounded wait on a TMA copy ran out in the SpMV kernel");
+    }
     count_launches((int64_t)hs->iter * g->kernels_per_iter);
     if (info) {
         info->iters = hs->iter;
@@ -1019,6 +1052,15 @@ static spg_status run_loop(spg_handle h, LoopGraph *g, int max_iter, IterState *
         info->ms = ms;
     }
     return SPG_OK;
+}
+
+static spg_status run_loop(spg_handle h, LoopGraph *g, int max_iter, IterState *hs,
+                           spg_iter_info *info, cudaStream_t s)
+{
+    spg_status st = launch_loop(h, g, max_iter, s);
+    if (st != SPG_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    return finish_loop(h, g, max_iter, hs, info);
 }
 
 extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int max_iter,
@@ -1041,7 +1083,7 @@ extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int 
         hs.zbuf[1] = h->z1.p;
         hs.inv_deg = h->fwd.d_inv_deg;
     }
-    CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
+    if ((st = upload_state(h, hs, s)) != SPG_OK) return st;
     if (p0) {
         const float *pd;
         if ((st = device_in(h, p0, N, &pd, s)) != SPG_OK) return st;
@@ -1059,13 +1101,14 @@ extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int 
     }, &g);
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
-    if ((st = run_loop(h, g, max_iter, &hs, info, s)) != SPG_OK) return st;
+    if ((st = launch_loop(h, g, max_iter, s)) != SPG_OK) return st;
     const bool out_host = !is_device_ptr(p_out);
     float *od = p_out;
     if (out_host) { CK(h->stage_out.ensure((size_t)N)); od = h->stage_out.p; }
     launch_scatter_state(N, h->fwd.d_inv, h->d_state, od, nullptr, 0, s);
     if (out_host) CK(cudaMemcpyAsync(p_out, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if ((st = finish_loop(h, g, max_iter, &hs, info)) != SPG_OK) return st;
     return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
 }
 
