@@ -53,9 +53,6 @@ constexpr int kStagedBlock = 1024;
 // measured best for each (R-MAT 22 PageRank iteration 0.192 ms at 4 vs
 // 0.198 at 5; banded SpMV 0.230 ms at 5 vs 0.240 at 4).
 constexpr int kPersistMinBlocks = 5;
-#ifndef SPG_L2_AHEAD
-#define SPG_L2_AHEAD 0
-#endif
 __host__ __device__ constexpr int persist_minb(int mode)
 {
     return (mode == EPI_RAW || mode == EPI_RAW_PAT) ? kPersistMinBlocks : 4;
@@ -456,10 +453,6 @@ template <> struct Slots<false> {
     __device__ __forceinline__ Slots(const PartView &pv, int64_t off) : p(pv.slab + off) {}
     __device__ __forceinline__ uint2 ld(int64_t i) const { return __ldcs(p + i); }
     __device__ __forceinline__ const char *bytes_at(int64_t i) const { return reinterpret_cast<const char *>(p + i); }
-    __device__ __forceinline__ void prefetch_l2(int64_t i) const
-    {
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(p + i));
-    }
 };
 template <> struct Slots<true> {
     static constexpr int kBytes = 4;
@@ -467,10 +460,6 @@ template <> struct Slots<true> {
     __device__ __forceinline__ Slots(const PartView &pv, int64_t off) : p(pv.slab4 + off) {}
     __device__ __forceinline__ uint2 ld(int64_t i) const { return make_uint2(__ldcs(p + i), 0x3f800000u); }
     __device__ __forceinline__ const char *bytes_at(int64_t i) const { return reinterpret_cast<const char *>(p + i); }
-    __device__ __forceinline__ void prefetch_l2(int64_t i) const
-    {
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(p + i));
-    }
 };
 
 // One workload (Solution 3) computed by the calling warp.
@@ -519,12 +508,6 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
                     for (st = 4; st + 4 <= nst; st += 4) {
                         if (pf.ahead) pf.advance((unsigned)(((int64_t)i * d.w + st * 32) * Slots<is_pattern(MODE)>::kBytes), lane);
                         const int64_t q = s + st * 32;
-#if SPG_L2_AHEAD
-                        if ((lane & 15) == 0 && st + 8 <= nst) {
-#pragma unroll
-                            for (int u = 4; u < 8; ++u) slab.prefetch_l2(s + (st + u) * 32);
-                        }
-#endif
                         const uint2 b0 = slab.ld(q), b1 = slab.ld(q + 32), b2 = slab.ld(q + 64), b3 = slab.ld(q + 96);
                         acc = slot_fma_g(a0, g, acc);
                         acc = slot_fma_g(a1, g, acc);
@@ -588,14 +571,6 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
                     uint2 a[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) a[u] = slab.ld(sa + (int64_t)(e + u) * 32);
-#if SPG_L2_AHEAD
-                    // the next 8 steps' lines into L2 while these 8 gather
-                    // (no registers held): lanes 0 and 16 cover each 256-byte step
-                    if ((lane & 15) == 0 && e + 15 < d.w) {
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) slab.prefetch_l2(sa + (int64_t)(e + 8 + u) * 32);
-                    }
-#endif
 #pragma unroll
                     for (int u = 0; u < 8; ++u) acc_a = slot_fma_g(a[u], g, acc_a);
                 }
