@@ -232,7 +232,7 @@ def run_secondary(args):
         rp, col = graph(args.workload)
         n, nnz = int(rp.shape[0] - 1), int(rp[-1])
         seeds = graphgen.pick_seeds(rp, 64, 4)
-        f = spg.Format(rp, col, kind="pagerank", vec_width=64)
+        f = spg.Format(rp, col, kind="pagerank", vec_width=64, loop_mode=1 if args.host_loop else 0)
         f.rwr(seeds, 0.15, tol=0.0, max_iter=args.warmup, like=like)
         L0 = spg.launch_count()
         with Clocks(0) as clk:
@@ -258,7 +258,7 @@ def run_secondary(args):
         rp, col = graph(args.workload)
         n, nnz = int(rp.shape[0] - 1), int(rp[-1])
         hits = args.workload == "hits22"
-        f = spg.Format(rp, col, kind="hits" if hits else "pagerank")
+        f = spg.Format(rp, col, kind="hits" if hits else "pagerank", loop_mode=1 if args.host_loop else 0)
         s = graphgen.pick_source(rp, 3)
         if hits:
             run = lambda k: f.hits(norm=2, iters=k, like=like)
@@ -303,7 +303,7 @@ def run_secondary(args):
         graphs = batch_graphs(512)
         nnz = sum(int(g[0][-1]) for g in graphs)
         n = sum(int(g[0].shape[0] - 1) for g in graphs)
-        b = spg.BatchFormat(graphs)
+        b = spg.BatchFormat(graphs, loop_mode=1 if args.host_loop else 0)
         b.pagerank(DAMPING, tol=0.0, max_iter=args.warmup, like=like)
         L0 = spg.launch_count()
         with Clocks(0) as clk:
@@ -329,7 +329,8 @@ def run_secondary(args):
         n, nnz = int(rp.shape[0] - 1), int(rp[-1])
         theta = torch.from_numpy(graphgen.normal(nnz, 7)).to(dev)
         s = graphgen.pick_source(rp, 3)
-        f = spg.Format(rp, col, val=theta.cpu().numpy(), kind="weighted", build_transpose=True)
+        f = spg.Format(rp, col, val=theta.cpu().numpy(), kind="weighted", build_transpose=True,
+                       loop_mode=1 if args.host_loop else 0)
         f.set_edge_logits(theta)
         r, _ = f.rwr_weighted(s, 0.15, 1e-10, 5000, like=theta)
         t_idx = torch.from_numpy(graphgen.pick_targets(rp, col, s, 1000, 5).astype(np.int64)).to(dev)
