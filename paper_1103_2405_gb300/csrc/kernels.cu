@@ -1007,10 +1007,7 @@ constexpr int kSpmmU = 8;
 // blocks per SM, per mode: the plain SpMM trades register rows for a third
 // block per SM (4.03 -> 3.76 ms at k = 64, R-MAT 22); the RWR epilogue needs
 // the registers (3.40 ms at 32 rows and two blocks, 5.2 ms at 16 and three).
-#ifndef SPG_SPMM_RWR_ROWS
-#define SPG_SPMM_RWR_ROWS 32
-#endif
-__host__ __device__ constexpr int spmm_rows(int mode) { return mode == EPI_RAW ? 16 : SPG_SPMM_RWR_ROWS; }
+__host__ __device__ constexpr int spmm_rows(int mode) { return mode == EPI_RAW ? 16 : 32; }
 __host__ __device__ constexpr int spmm_minb(int mode) { return mode == EPI_RAW ? 3 : 2; }
 // Rows whose epilogue operands are fetched together.
 constexpr int kSpmmEpi = 4;
