@@ -92,13 +92,6 @@ struct FSum {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
-// One stored slot: padding has col = -1 and contributes nothing (no gather).
-__device__ __forceinline__ float slot_fma(uint2 v, const float *__restrict__ x, float acc)
-{
-    const int c = (int)v.x;
-    const float xv = c >= 0 ? __ldg(x + c) : 0.0f;
-    return fmaf(__uint_as_float(v.y), xv, acc);
-}
 
 // Uniform per-launch epilogue parameters, read once from the state.
 struct Epi {
@@ -208,14 +201,6 @@ __device__ __forceinline__ void finish_split(const Epi &E, const SplitView &sv, 
         red[sv.red_split_base + sr.red_slot] = make_double2(r0.value(), r1.value());
 }
 
-template <int MODE>
-__device__ __forceinline__ void finish_row(const Epi &E, const SplitView &sv, double2 *red,
-                                           uint32_t rid, float acc, const float *__restrict__ x,
-                                           float *__restrict__ y, FSum &r0, FSum &r1)
-{
-    if (rid & kRowSplit) finish_split<MODE>(E, sv, red, rid, acc, x, y);
-    else epilogue<MODE>(E, rid, acc, x, y, r0, r1);
-}
 
 // What a row's epilogue reads besides its sum, fetched before the sum is
 // computed so the loads overlap the slot stream: the row entry, y_v (rows
