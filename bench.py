@@ -612,6 +612,14 @@ def main():
             ablation[name] = {"kernel_ms": float(fa.time_parts(mode=1, reps=20).sum()),
                               "predicted_ms": ia["predicted_ms"], "padded_slots": ia["padded_slots"]}
             del fa
+        # claim order of the persistent kernel: the default (longest first
+        # by dependent memory round trips) against the ranking order
+        fo = spg.Format(rp, col, kind="pagerank", claim_order=1)
+        fo.pagerank(DAMPING, tol=0.0, max_iter=3, like=like)
+        ablation["ranking_claim_order"] = {"kernel_ms": float(fo.time_parts(mode=1, reps=20).sum()),
+                                           "predicted_ms": fo.info()["predicted_ms"],
+                                           "padded_slots": fo.info()["padded_slots"]}
+        del fo
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -379,8 +379,8 @@ static int64_t round_up32(int64_t v) { return (v + 31) / 32 * 32; }
 
 /* Storage decision of Section 3.1, Solution 3 for a w x h workload:
  * rule 0 (the paper): row-major when w >= h, else column-major.
- * rule 1 (GB300 reading): the major with fewer padded slots, row-major on a
- * tie.  Row-major pads w to a multiple of 32, column-major pads h.
+ * rule 1 (GB300 reading): the major with fewer padded slots, column-major
+ * on a tie.  Row-major pads w to a multiple of 32, column-major pads h.
  * rules 2 and 3: every workload row-major (CSR-vector) or column-major
  * (ELL) -- the special cases of the composite format named in Section 5. */
 static int pick_major(int rule, int64_t w, int64_t h)
@@ -389,7 +389,7 @@ static int pick_major(int rule, int64_t w, int64_t h)
     if (rule == 2) return 0;
     if (rule == 3) return 1;
     int64_t row_slots = h * round_up32(w), col_slots = round_up32(h) * w;
-    return row_slots <= col_slots ? 0 : 1;
+    return row_slots < col_slots ? 0 : 1;
 }
 
 /*

@@ -46,7 +46,8 @@ class _Opts(ctypes.Structure):
                 ("slab_prefetch", ctypes.c_int64), ("loop_mode", ctypes.c_int),
                 ("max_rows", ctypes.c_int64), ("kernel", ctypes.c_int), ("pattern_only", ctypes.c_int),
                 ("row_part", ctypes.c_void_p), ("part_id", ctypes.c_int32), ("nparts", ctypes.c_int32),
-                ("unit_slots", ctypes.c_int64), ("separate_check", ctypes.c_int32)]
+                ("unit_slots", ctypes.c_int64), ("separate_check", ctypes.c_int32),
+                ("claim_order", ctypes.c_int32)]
 
 
 class IterInfo(ctypes.Structure):
@@ -204,7 +205,7 @@ class Format:
                  keep_csr=False, host_only=False, split_cost=0.0, table=None, x_stage_cols=0,
                  slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, pattern_only=False,
                  row_part=None, part_id=0, nparts=None, unit_slots=0, separate_check=False,
-                 stream=None):
+                 claim_order=0, stream=None):
         L = lib()
         self._h = ctypes.c_void_p(None)
         on_dev = _is_torch(rowptr) and rowptr.is_cuda
@@ -228,6 +229,7 @@ class Format:
                      int(bool(pattern_only)))
         opts.unit_slots = int(unit_slots)
         opts.separate_check = int(bool(separate_check))
+        opts.claim_order = int(claim_order)
         if row_part is not None:
             row_part = np.ascontiguousarray(row_part, dtype=np.int32)
             opts.row_part = row_part.ctypes.data
@@ -458,7 +460,7 @@ class BatchFormat:
 
     def __init__(self, graphs, heavy_row=-1, layout_rule=1, max_warps=0, x_stage_cols=0,
                  slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, host_only=False, table=None,
-                 stream=None):
+                 claim_order=0, stream=None):
         L = lib()
         keep = []
         arr = (_Csr * len(graphs))()
@@ -474,6 +476,7 @@ class BatchFormat:
                      -1 if host_only else 0, 0.0, None if tpath is None else str(tpath).encode(),
                      int(x_stage_cols), int(slab_prefetch), int(loop_mode), int(max_rows),
                      int(kernel), 0)
+        opts.claim_order = int(claim_order)
         self._h = ctypes.c_void_p(None)
         _check(L.spg_build_batch(ctypes.cast(arr, ctypes.c_void_p), len(graphs), ctypes.byref(opts),
                                  _stream(stream), ctypes.byref(self._h)))

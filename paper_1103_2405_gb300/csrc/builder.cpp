@@ -14,6 +14,7 @@
 //      rectangles of w = first row's length and h = floor(WL / w) rows, row-
 //      or column-major with w (or h) padded to a multiple of 32 (Solution 3).
 // Host C++ with std::thread; nothing here runs on the GPU.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -133,7 +134,7 @@ static inline int pick_major(int rule, int64_t w, int64_t h)
     if (rule == 0) return w >= h ? 0 : 1;                 // the paper's rule
     if (rule == 2) return 0;                              // every workload CSR-vector
     if (rule == 3) return 1;                              // every workload ELL
-    return h * ru32(w) <= ru32(h) * w ? 0 : 1;            // fewer padded slots
+    return h * ru32(w) < ru32(h) * w ? 0 : 1;             // fewer padded slots; tie: column-major
 }
 
 // Rows of a workload starting at a row of length w: floor(WL / w), at least
@@ -147,6 +148,66 @@ static inline int64_t wl_height(int64_t WL, int64_t w, int64_t left, int64_t max
     if (max_rows > 0 && h > max_rows) h = max_rows;
     if (h > left) h = left;
     return h;
+}
+
+double latency_rounds(const Workload &d)
+{
+    if (d.w == 0) return 1.0 + 2.0 * (double)((d.h + 127) / 128);
+    if (d.major == 1) {
+        const int64_t hp = ru32(d.h);
+        int64_t r = 0;
+        for (int64_t b = 0; b < hp; b += 64)
+            r += b + 32 < hp ? 2 * ((d.w + 3) / 4) : 2 * (d.w / 8) + (d.w % 8 ? 2 : 0);
+        return 2.0 + (double)std::max<int64_t>(r, 2);
+    }
+    const int64_t nst = d.w / 32;
+    const int64_t per = (nst >= 4 ? nst / 4 + 1 : 0) + (nst % 4 ? 2 : 0);
+    return 2.0 + (double)d.h * (double)per;
+}
+
+// Claim cost of a workload: padded slots + 4 per row (a row-free workload:
+// 4 per row).
+static inline int64_t claim_cost(const Workload &d)
+{
+    const int64_t slots = d.w == 0 ? 0 : d.major == 0 ? (int64_t)d.h * d.w : ru32(d.h) * d.w;
+    return slots + 4 * (int64_t)d.h;
+}
+
+// Claim order and claim units of every part.  The persistent kernels'
+// warps take work in array order, so a long workload that comes late in the
+// array keeps one warp busy after the others have run out of work (R-MAT
+// scale 22 in ranking order with 32 x 32 workloads stored row-major: claimed
+// at 105 us of a 190 us launch, each ran about 80 us).  Longest first
+// (stable, by latency_rounds) ends the launch with the short ones.  Claim
+// units are then runs of consecutive workloads whose cost reaches
+// unit_slots, so that one atomic on the work counter covers several small
+// workloads while a large one stays alone.
+static void order_and_group(Layout &L, const BuildParams &prm)
+{
+    if (prm.claim_order == 0 && !L.wl.empty()) {
+        for (const PartHost &ph : L.parts) {
+            auto b = L.wl.begin() + ph.wl_off;
+            std::vector<std::pair<double, Workload>> key((size_t)ph.nwl_total);
+            for (int64_t j = 0; j < ph.nwl_total; ++j) key[(size_t)j] = {latency_rounds(b[j]), b[j]};
+            std::stable_sort(key.begin(), key.end(),
+                             [](const std::pair<double, Workload> &a, const std::pair<double, Workload> &c) {
+                                 return a.first > c.first;
+                             });
+            for (int64_t j = 0; j < ph.nwl_total; ++j) b[j] = key[(size_t)j].second;
+        }
+    }
+    L.units.clear();
+    for (PartHost &ph : L.parts) {
+        ph.unit_off = (int64_t)L.units.size();
+        int64_t acc = 0;
+        for (int64_t j = 0; j < ph.nwl_total; ++j) {
+            if (acc == 0) L.units.push_back((int32_t)j);
+            acc += L.wl.empty() ? 1 : claim_cost(L.wl[(size_t)(ph.wl_off + j)]);
+            if (prm.unit_slots <= 1 || acc >= prm.unit_slots) acc = 0;
+        }
+        ph.nunits = (int64_t)L.units.size() - ph.unit_off;
+        L.units.push_back((int32_t)ph.nwl_total);
+    }
 }
 
 // Algorithm 3: walk the ranked rows workload by workload; every max_warps
@@ -508,31 +569,6 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
         nblocks_all += ph.nblocks;
     }
     if (nwl_all > INT32_MAX || nrows_all > INT32_MAX) { err = "layout too large"; return false; }
-    // claim units: runs of consecutive workloads of one part whose cost
-    // (padded slots + 4 per row) reaches unit_slots, so that a warp's one
-    // claim on the work counter covers several small workloads while a
-    // large one stays alone
-    L.units.clear();
-    for (int64_t p = 0; p < P; ++p) {
-        PartHost &ph = L.parts[(size_t)p];
-        ph.unit_off = (int64_t)L.units.size();
-        const int64_t zr = (int64_t)L.zero_rows.size();
-        int64_t acc = 0;
-        for (int64_t j = 0; j < ph.nwl_total; ++j) {
-            int64_t cost;
-            if (j < ph.nwl) {
-                const int64_t w = ww[p][(size_t)j], h = wh[p][(size_t)j];
-                cost = (wm[p][(size_t)j] == 0 ? h * ru32(w) : ru32(h) * w) + 4 * h;
-            } else {
-                cost = 4 * std::min<int64_t>(kZeroRowsPerWorkload, zr - (j - ph.nwl) * kZeroRowsPerWorkload);
-            }
-            if (acc == 0) L.units.push_back((int32_t)j);
-            acc += cost;
-            if (prm.unit_slots <= 1 || acc >= prm.unit_slots) acc = 0;
-        }
-        ph.nunits = (int64_t)L.units.size() - ph.unit_off;
-        L.units.push_back((int32_t)ph.nwl_total);
-    }
     L.padded_slots = nslab;
     L.wl.resize((size_t)nwl_all);
     L.rows.resize((size_t)nrows_all);
@@ -681,6 +717,7 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
         rank_chunk[p].clear(); rank_chunk[p].shrink_to_fit();
         rank_len[p].clear(); rank_len[p].shrink_to_fit();
     }
+    order_and_group(L, prm);
     return true;
 }
 

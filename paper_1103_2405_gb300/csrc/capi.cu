@@ -410,6 +410,8 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
             return fail(SPG_ERR_INVALID, "pattern_only needs a PAGERANK handle");
         prm.pattern_only = o.pattern_only != 0;
         prm.unit_slots = o.unit_slots > 0 ? o.unit_slots : kDefaultUnitSlots;
+        if (o.claim_order < 0 || o.claim_order > 1) return fail(SPG_ERR_INVALID, "claim_order must be 0 or 1");
+        prm.claim_order = o.claim_order;
         std::vector<uint8_t> rkeep;
         if (o.row_part) {
             if (kind != SPG_KIND_PAGERANK) return fail(SPG_ERR_INVALID, "row_part needs a PAGERANK handle");
@@ -1675,6 +1677,8 @@ extern "C" spg_status spg_build_batch(const spg_csr *graphs, int count,
         prm.max_warps = o.max_warps > 0 ? o.max_warps : (h->host_only ? 9728 : query_max_warps());
         prm.max_rows = o.max_rows < 0 ? 0 : (o.max_rows > 0 ? o.max_rows : kDefaultMaxRows);
         prm.unit_slots = o.unit_slots > 0 ? o.unit_slots : kDefaultUnitSlots;
+        if (o.claim_order < 0 || o.claim_order > 1) return fail(SPG_ERR_INVALID, "claim_order must be 0 or 1");
+        prm.claim_order = o.claim_order;
         if (o.split_cost > 0) prm.split_cost = o.split_cost;
         prm.keep_plan = o.keep_plan != 0;
         prm.seg_off = h->goff.data();

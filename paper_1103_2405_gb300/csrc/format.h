@@ -46,7 +46,18 @@ struct BuildParams {
     // until their cost (padded slots + 4 per row) reaches this; <= 1 = one
     // workload per unit
     int64_t unit_slots = 0;
+    // 0: workloads of a part stored (and claimed) longest first by
+    // latency_rounds(); 1: in the ranking order
+    int claim_order = 0;
 };
+
+// Dependent global-memory round trips of the warp that computes workload d
+// in the SpMV kernels' loops: descriptor and row operands, then per
+// 32-row block of a column-major workload two trips (slots, then gathers)
+// per batch of 8 columns (4 when two blocks run together), per row of a
+// row-major workload one trip per 4 pipelined 32-slot steps plus two for
+// the rest; a row-free workload two trips per 128 rows.
+double latency_rounds(const Workload &d);
 
 struct PartHost {
     int64_t c0 = 0, c1 = 0;

@@ -1665,7 +1665,9 @@ void launch_batch_reduce(IterState *st, int nchunk, cudaStream_t s)
 
 // Per graph: the next base (c * dangling mass + 1 - c) / n_g and the
 // iteration its L1 change first went below tol; the loop stops when every
-// graph has converged or at max_iter.
+// graph has converged (its L1 change has gone below tol once: an FP32
+// iterate can settle into a rounding cycle whose change stays near tol) or
+// at max_iter.
 __global__ void __launch_bounds__(1024) k_batch_check(IterState *st, int ngraph,
                                                       cudaGraphConditionalHandle cond, int use_cond)
 {
@@ -1687,11 +1689,8 @@ __global__ void __launch_bounds__(1024) k_batch_check(IterState *st, int ngraph,
         st->gdelta[g] = dg;
         const double ng = (double)(st->goff[g + 1] - st->goff[g]);
         st->gbase[g] = (float)((c * dg + (1.0 - c)) / ng);
-        if (tol > 0.0 && l1 < tol) {
-            if (st->giters[g] == 0) st->giters[g] = it;
-        } else {
-            all = 0;
-        }
+        if (tol > 0.0 && l1 < tol && st->giters[g] == 0) st->giters[g] = it;
+        if (st->giters[g] == 0) all = 0;
         mx = fmax(mx, l1);
     }
     for (int o = 16; o > 0; o >>= 1) {

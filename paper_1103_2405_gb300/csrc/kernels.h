@@ -48,12 +48,13 @@ void launch_part_spmm(int mode, const PartView &pv, const SplitView &sv, const f
 // (when cond != 0) to "keep iterating".
 void launch_check(int mode, IterState *st, const double2 *red, int nred,
                   unsigned long long cond, int use_cond, cudaStream_t s);
-// Same for SpMM RWR: per-column l1_k / delta_k, l1 = max over columns.
 // Row-partitioned PageRank on one device: all-gather of the ranks' rows and
 // the all-reduce / check over all ranks' partials.
 void launch_allgather_rows(int64_t n, const int8_t *owner, IterState *const *states, int P, bool pat,
                            cudaStream_t s);
 void launch_check_ranks(IterState *const *states, int P, const double2 *red, int nred, cudaStream_t s);
+// The check for SpMM RWR: per-column l1_k / delta_k (two-stage column sums
+// in `scratch`), l1 = max over columns.
 void launch_check_k(IterState *st, const double *redk, int nred, int k, double *delta_k,
                     double *l1_k, double *scratch, unsigned long long cond, int use_cond,
                     cudaStream_t s);
@@ -116,14 +117,16 @@ void launch_edge_grad(int64_t n, const int64_t *a_rp, const int32_t *a_col, cons
                       const float *lambda, const float *r, float c, float *dtheta,
                       const int32_t *heavy, int nheavy, cudaStream_t s);
 
-// Resident blocks per SM of the tiled-composite SpMV kernel on this device.
-// Resident blocks per SM of the persistent plain SpMV kernel (kernel option 4).
+// Resident blocks per SM of the persistent 8-warp SpMV kernel (options 0
+// and 4) and of the plain one-warp-per-workload kernel (option 2) on this
+// device.
 int persist_blocks_per_sm();
 int part_blocks_per_sm();
 
-// Batch of graphs: per-graph L1 change and dangling mass (one block per
-// graph, fixed order), then the per-graph bases, convergence record and the
-// loop condition (one block).
+// Batch of graphs: L1 change and dangling mass per chunk of a graph's rows
+// (nchunk chunks, one block each), then the per-graph sums of the chunks in
+// order, the per-graph bases, convergence record and the loop condition
+// (one block).
 void launch_batch_reduce(IterState *st, int nchunk, cudaStream_t s);
 void launch_batch_check(IterState *st, int ngraph, unsigned long long cond, int use_cond,
                         cudaStream_t s);

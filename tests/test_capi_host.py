@@ -236,3 +236,21 @@ def test_rank_formats_hold_their_rows(spg):
         kw.update(bad)
         with pytest.raises(spg.SpgError):
             spg.Format(rp, col, **kw)
+
+
+def test_claim_order_option_keeps_the_stored_entries(spg):
+    # the claim order permutes whole workloads: the stored entries, their
+    # values and the zero rows are the same in both orders; other values
+    # are refused
+    rp, col = graphgen.rmat(12, 8, seed=4)
+    keys = []
+    for order in (0, 1):
+        f = spg.Format(rp, col, kind="pagerank", host_only=True, max_warps=200, claim_order=order)
+        r, c, v = f.export_entries()
+        o = np.lexsort((c, r))
+        keys.append((r[o], c[o], v[o].view(np.uint32), f.zero_rows(), f.info()["padded_slots"]))
+    for other in keys[1:]:
+        for a, b in zip(keys[0], other):
+            assert np.array_equal(a, b)
+    with pytest.raises(spg.SpgError):
+        spg.Format(rp, col, kind="pagerank", host_only=True, claim_order=2)

@@ -41,6 +41,24 @@ def test_pagerank_matches_oracle(g14, opts):
     assert info["last_l1"] < 1e-8
 
 
+@pytest.mark.parametrize("opts", [dict(), dict(tile_width=2048, heavy_row=32), dict(unit_slots=1)])
+def test_claim_order_does_not_change_the_result(g14, opts):
+    # longest-first and ranking-order claims: every row has one writer and
+    # split rows combine in chunk order, so the iterates agree bit for bit
+    rp, col, M, p_star = g14
+    like = torch.empty(0, device=DEV)
+    got = []
+    for order in (0, 1):
+        f = spg.Format(rp, col, kind="pagerank", claim_order=order, **opts)
+        p, info = f.pagerank(C, tol=1e-8, max_iter=1000, like=like)
+        x = torch.from_numpy(graphgen.uniform(rp.shape[0] - 1, 3)).to(DEV)
+        got.append((p.cpu(), info["iters"], f.spmv(x).cpu()))
+    for other in got[1:]:
+        assert torch.equal(got[0][0], other[0]) and got[0][1] == other[1]
+        assert torch.equal(got[0][2], other[2])
+    assert np.abs(got[0][0].numpy().astype(np.float64) - p_star).sum() <= 1e-6
+
+
 def test_pagerank_warm_start_and_limits(g14):
     rp, col, M, p_star = g14
     f = spg.Format(rp, col, kind="pagerank")

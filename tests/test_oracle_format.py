@@ -125,7 +125,7 @@ def test_partition_covers_every_nonzero_once_with_heavy_split():
         assert w == part["rank_len"][f]
         assert h == min(max(1, part["WL"] // w), len(part["rank_len"]) - f)
         rs, cs = h * ((w + 31) // 32 * 32), (h + 31) // 32 * 32 * w
-        assert mj == (0 if rs <= cs else 1)
+        assert mj == (0 if rs < cs else 1)
         pos += h
     assert pos == len(part["rank_len"])
 
@@ -196,3 +196,18 @@ def test_forced_storage_rules_are_the_special_cases(rule, major):
     assert np.all(np.asarray(part["wl_major"]) == major)
     for k in ("rank_row", "rank_len", "wl_first", "wl_h", "wl_w"):
         assert np.array_equal(np.asarray(part[k]), np.asarray(base[k]))
+
+
+@pytest.mark.parametrize("w,h", [(32, 32), (64, 32), (16, 16)])
+def test_rule1_tie_goes_to_column_major(w, h):
+    # h rows of w entries and WL = w * h: one w x h workload whose row-major
+    # and column-major forms pad to the same number of slots; rule 1 then
+    # stores it column-major (its rows side by side), the paper's rule
+    # (w >= h) row-major
+    ids = np.arange(h, dtype=np.int64)
+    rl = np.full(h, w, np.int64)
+    for rule, major in ((1, 1), (0, 0)):
+        part = oracle.partition_tile(ids, rl, heavy=0, wl=w * h, max_warps=8, rule=rule,
+                                     table=_const_table())
+        assert list(part["wl_h"]) == [h] and list(part["wl_w"]) == [w]
+        assert list(part["wl_major"]) == [major]
