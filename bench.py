@@ -29,6 +29,8 @@ DAMPING = 0.85
 WORKLOADS = {
     "rmat22": dict(scale=22, ef=16, desc="R-MAT scale 22, edge factor 16, PageRank iteration"),
     "rmat26": dict(scale=26, ef=16, desc="R-MAT scale 26, edge factor 16, PageRank iteration"),
+    "rmat24": dict(scale=24, ef=16, desc="R-MAT scale 24, edge factor 16, PageRank iteration "
+                                         "(the largest R-MAT a full kernel profile covers)"),
     "chunglu50m": dict(cl=(50_000_000, 800_000_000, 2.1, 1_000_000),
                        desc="Chung-Lu 50M nodes, ~800M edges, exponent 2.1, max degree 1M, "
                             "PageRank iteration"),
