@@ -254,3 +254,28 @@ def test_claim_order_option_keeps_the_stored_entries(spg):
             assert np.array_equal(a, b)
     with pytest.raises(spg.SpgError):
         spg.Format(rp, col, kind="pagerank", host_only=True, claim_order=2)
+
+
+def test_claim_order_puts_the_longest_latency_chain_first(spg):
+    # every workload row-major (rule 2), WL = 64: the rows of length 64 form
+    # one-row workloads (a 2-step row: few round trips), the rows of length
+    # 2 form 32-row workloads (32 rows walked one after another: many).
+    # Ranking order stores the long rows first; longest-first stores the
+    # 32-row workloads first.  Entries are exported in storage order.
+    n = 200
+    edges = [(u, v) for v in range(4) for u in range(100, 164)]
+    edges += [(u, v) for v in range(4, 68) for u in (100, 101)]
+    edges.sort()
+    src = np.array([e[0] for e in edges], np.int64)
+    col = np.array([e[1] for e in edges], np.int32)
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, src + 1, 1)
+    rp = np.cumsum(rp)
+    first = {}
+    for order in (0, 1):
+        f = spg.Format(rp, col, kind="pagerank", host_only=True, wl=64, heavy_row=0, layout_rule=2,
+                       max_warps=64, claim_order=order)
+        r, c, v = f.export_entries()
+        first[order] = int(r[0])
+    assert first[1] in range(4)          # ranking order: a row of length 64
+    assert first[0] in range(4, 68)      # longest first: a 32-row workload of 2-entry rows
