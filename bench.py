@@ -4,12 +4,13 @@ Workload (default): R-MAT scale 22 (4,194,304 nodes), edge factor 16, R-MAT
 (a, b, c, d) = (0.57, 0.19, 0.19, 0.05), duplicates and self-loops removed,
 seed 1, seeded node relabel; M = W^T with FP32 values 1/outdeg.  One step =
 one PageRank iteration (Eq. 6): the tiled-composite SpMV with the fused
-damping / teleport / dangling / L1 epilogue plus the check kernel, run inside
+damping / teleport / dangling / L1 epilogue and convergence check, run inside
 the library's CUDA-graph loop.  Metric: GFLOP/s = 2 nnz per step.
 
 The matrix stream (~0.5 GB) is larger than the 126 MB L2, so no flush runs
 between steps.  Printed as ONE JSON line on rank 0.  `--impl reference` times
-the FP64 oracle (the reference of this build) on the host cores instead.
+the FP64 oracle (the plain single-threaded restatement of the method that the
+GPU results are checked against) on the host cores instead.
 """
 from __future__ import annotations
 
