@@ -202,6 +202,12 @@ typedef struct {
      * the orders agree within 0.3 % (R-MAT 22 0.1755 vs 0.1760 ms, R-MAT 24
      * 0.798 vs 0.800 ms, Chung-Lu 4M 0.1661 vs 0.1657 ms). */
     int32_t claim_order;
+    /* Non-zero: also store every part as a row-sorted (row, column, value)
+     * list -- the paper's TILE-COO format (same degree order and column
+     * tiles, COO storage instead of the composite one; Section 5 compares
+     * the two) -- for spg_spmv_tile_coo.  12 more bytes per non-zero on the
+     * device.  Ignored by spg_build_batch. */
+    int32_t tile_coo;
 } spg_build_opts;
 
 /* Per-call results of the power iterations. */
@@ -293,6 +299,16 @@ spg_status spg_spmv(spg_handle h, const float *x, float *y, float alpha, float b
 /* Same product with x and y already in the handle's permuted order (device
  * pointers only): y' = M' x', no permutation passes. */
 spg_status spg_spmv_permuted(spg_handle h, const float *x_perm, float *y_perm, void *stream);
+
+/* TILE-COO SpMV (Section 5: the tiled kernel with COO storage, the ablation
+ * of the composite storage): y' = M' x' on PERMUTED device vectors of n
+ * floats (x' = x[inv], as spg_spmv_permuted), one launch per part over its
+ * row-sorted entry list: each warp takes 256 consecutive entries, sums
+ * them per row with a segmented warp scan and adds rows that may continue
+ * into a neighbouring warp's entries with atomicAdd (the summation order
+ * of such rows is not fixed).  y' is zeroed first.  Needs a handle built
+ * with tile_coo != 0 (else SPG_ERR_INVALID); x' and y' must be distinct. */
+spg_status spg_spmv_tile_coo(spg_handle h, const float *x_perm, float *y_perm, void *stream);
 
 /* Y = alpha * M X + beta * Y for k vectors: X (n x k) and Y (n x k) FP32,
  * row-major with leading dimensions ldx, ldy >= k, original row order.

@@ -47,7 +47,7 @@ class _Opts(ctypes.Structure):
                 ("max_rows", ctypes.c_int64), ("kernel", ctypes.c_int), ("pattern_only", ctypes.c_int),
                 ("row_part", ctypes.c_void_p), ("part_id", ctypes.c_int32), ("nparts", ctypes.c_int32),
                 ("unit_slots", ctypes.c_int64), ("separate_check", ctypes.c_int32),
-                ("claim_order", ctypes.c_int32)]
+                ("claim_order", ctypes.c_int32), ("tile_coo", ctypes.c_int32)]
 
 
 class IterInfo(ctypes.Structure):
@@ -79,7 +79,7 @@ EXPORTS = ["spg_build_format", "spg_destroy", "spg_format_info", "spg_tile_info"
            "spg_batch_offsets", "spg_batch_pagerank",
            "spg_baseline_spmv", "spg_baseline_pagerank", "spg_time_parts", "spg_load_table", "spg_launch_count",
            "spg_status_string", "spg_last_error", "spg_version", "spg_spmv_permuted_noalloc",
-           "spg_partition_rows", "spg_pagerank_ranks"]
+           "spg_partition_rows", "spg_pagerank_ranks", "spg_spmv_tile_coo"]
 
 _lib = None
 
@@ -104,6 +104,7 @@ def lib():
             "spg_format_zero_rows": [P, P],
             "spg_spmv": [P, P, P, f32, f32, P],
             "spg_spmv_permuted": [P, P, P, P],
+            "spg_spmv_tile_coo": [P, P, P, P],
             "spg_spmm": [P, P, i64, P, i64, i32, f32, f32, P],
             "spg_pagerank": [P, f32, f64, i32, P, P, ctypes.POINTER(IterInfo), P],
             "spg_rwr": [P, f32, P, i32, f64, i32, P, ctypes.POINTER(IterInfo), P],
@@ -205,7 +206,7 @@ class Format:
                  keep_csr=False, host_only=False, split_cost=0.0, table=None, x_stage_cols=0,
                  slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, pattern_only=False,
                  row_part=None, part_id=0, nparts=None, unit_slots=0, separate_check=False,
-                 claim_order=0, stream=None):
+                 claim_order=0, tile_coo=False, stream=None):
         L = lib()
         self._h = ctypes.c_void_p(None)
         on_dev = _is_torch(rowptr) and rowptr.is_cuda
@@ -230,6 +231,7 @@ class Format:
         opts.unit_slots = int(unit_slots)
         opts.separate_check = int(bool(separate_check))
         opts.claim_order = int(claim_order)
+        opts.tile_coo = int(bool(tile_coo))
         if row_part is not None:
             row_part = np.ascontiguousarray(row_part, dtype=np.int32)
             opts.row_part = row_part.ctypes.data
@@ -309,6 +311,11 @@ class Format:
 
     def spmv_permuted(self, xp, yp, stream=None):
         _check(lib().spg_spmv_permuted(self._h, _ptr(xp)[0], _ptr(yp)[0], _stream(stream)))
+        return yp
+
+    def spmv_tile_coo(self, xp, yp, stream=None):
+        """TILE-COO SpMV on permuted device vectors (handle built with tile_coo)."""
+        _check(lib().spg_spmv_tile_coo(self._h, _ptr(xp)[0], _ptr(yp)[0], _stream(stream)))
         return yp
 
     def spmm(self, X, Y=None, alpha=1.0, beta=0.0, stream=None):

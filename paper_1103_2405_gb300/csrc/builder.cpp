@@ -546,6 +546,33 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
     for (int64_t r = 0; r < N; ++r)
         if (first_part[(size_t)r] < 0 && kept(L.inv[(size_t)r])) L.zero_rows.push_back(r);
 
+    // TILE-COO: the same degree order and column tiles, each part's entries
+    // as a plain (row, column, value) list in row order
+    if (prm.build_coo) {
+        L.coo_off.assign((size_t)P + 1, 0);
+        for (int64_t p = 0; p < P; ++p) L.coo_off[(size_t)p + 1] = L.coo_off[(size_t)p] + L.parts[(size_t)p].nnz;
+        const int64_t tot = L.coo_off[(size_t)P];
+        L.coo_row.resize((size_t)tot);
+        L.coo_col.resize((size_t)tot);
+        L.coo_val.resize((size_t)tot);
+        std::vector<int64_t> pos((size_t)N + 1);
+        for (int64_t p = 0; p < P; ++p) {
+            pos[0] = L.coo_off[(size_t)p];
+            for (int64_t r = 0; r < N; ++r) pos[(size_t)r + 1] = pos[(size_t)r] + part_start(p + 1, r) - part_start(p, r);
+            parallel_for(N, 1 << 14, [&](int64_t lo, int64_t hi) {
+                for (int64_t r = lo; r < hi; ++r) {
+                    const int64_t b = part_start(p, r), e = part_start(p + 1, r);
+                    for (int64_t k = b; k < e; ++k) {
+                        const int64_t q = pos[(size_t)r] + (k - b);
+                        L.coo_row[(size_t)q] = (int32_t)r;
+                        L.coo_col[(size_t)q] = mcol[(size_t)k];
+                        L.coo_val[(size_t)q] = mval[(size_t)k];
+                    }
+                }
+            });
+        }
+    }
+
     // 5. packing: offsets.  The rows without entries (the epilogue alone)
     // go with part 0, the first and largest launch: there they are claimed
     // last, as filler while its long workloads finish, instead of forming a
@@ -755,6 +782,11 @@ cudaError_t upload_layout(Layout &L, bool keep_host, cudaStream_t s)
     SPG_UP(d_split, split);
     SPG_UP(d_slot_owner, slot_owner);
     if (!L.edge_slot.empty()) SPG_UP(d_edge_slot, edge_slot);
+    if (!L.coo_off.empty()) {
+        SPG_UP(d_coo_row, coo_row);
+        SPG_UP(d_coo_col, coo_col);
+        SPG_UP(d_coo_val, coo_val);
+    }
 #undef SPG_UP
     size_t pb = std::max<int64_t>(1, L.nchunk_slots) * sizeof(float);
     if ((e = cudaMalloc((void **)&L.d_partial, pb)) != cudaSuccess) return e;
@@ -770,6 +802,9 @@ cudaError_t upload_layout(Layout &L, bool keep_host, cudaStream_t s)
         std::vector<uint32_t>().swap(L.rows);
         std::vector<uint2>().swap(L.slab);
         std::vector<uint32_t>().swap(L.slab4);
+        std::vector<int32_t>().swap(L.coo_row);
+        std::vector<int32_t>().swap(L.coo_col);
+        std::vector<float>().swap(L.coo_val);
     }
     return cudaSuccess;
 }
@@ -779,6 +814,8 @@ void Layout::free_device()
     cudaFree(d_perm); cudaFree(d_inv); cudaFree(d_wl); cudaFree(d_units); cudaFree(d_rows); cudaFree(d_slab);
     cudaFree(d_split); cudaFree(d_slot_owner); cudaFree(d_partial); cudaFree(d_counter);
     cudaFree(d_edge_slot); cudaFree(d_slab4); cudaFree(d_inv_deg);
+    cudaFree(d_coo_row); cudaFree(d_coo_col); cudaFree(d_coo_val);
+    d_coo_row = d_coo_col = nullptr; d_coo_val = nullptr;
     d_slab4 = nullptr; d_inv_deg = nullptr;
     d_perm = d_inv = nullptr; d_wl = nullptr; d_units = nullptr; d_rows = nullptr; d_slab = nullptr;
     d_split = nullptr; d_slot_owner = nullptr; d_partial = nullptr; d_counter = nullptr;

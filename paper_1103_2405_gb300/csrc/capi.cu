@@ -412,6 +412,7 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
         prm.unit_slots = o.unit_slots > 0 ? o.unit_slots : kDefaultUnitSlots;
         if (o.claim_order < 0 || o.claim_order > 1) return fail(SPG_ERR_INVALID, "claim_order must be 0 or 1");
         prm.claim_order = o.claim_order;
+        prm.build_coo = o.tile_coo != 0;
         std::vector<uint8_t> rkeep;
         if (o.row_part) {
             if (kind != SPG_KIND_PAGERANK) return fail(SPG_ERR_INVALID, "row_part needs a PAGERANK handle");
@@ -544,6 +545,7 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
                     for (int64_t u = 0; u < n; ++u) dcls[(size_t)u] = rp[u + 1] == rp[u] ? 1 : 0;
                     ts.row_class = dcls.data();
                     h->bwd.reset(new Layout());
+                    prm.build_coo = false;
                     if (!build_layout(ts, prm, *h->bwd, err)) return fail(SPG_ERR_INVALID, err);
                     cudaError_t e = upload_layout(*h->bwd, o.keep_plan != 0, s);
                     if (e != cudaSuccess) return cuda_fail(e, "upload transpose");
@@ -852,6 +854,21 @@ extern "C" spg_status spg_spmv_permuted(spg_handle h, const float *xp, float *yp
         xp = h->x.p;
     }
     launch_parts(h, EPI_RAW, xp, yp, nullptr, nullptr, s);
+    CK(cudaGetLastError());
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_spmv_tile_coo(spg_handle h, const float *xp, float *yp, void *stream)
+{
+    if (!h || h->host_only) return fail(SPG_ERR_INVALID, "no device format");
+    if (!xp || !yp || xp == yp) return fail(SPG_ERR_INVALID, "x and y must be distinct device vectors");
+    const Layout &L = h->fwd;
+    if (L.coo_off.size() < 2 || !L.d_coo_row) return fail(SPG_ERR_INVALID, "build the handle with tile_coo");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(yp, 0, (size_t)L.n * sizeof(float), s));
+    for (size_t p = 0; p + 1 < L.coo_off.size(); ++p)
+        launch_tile_coo(L.d_coo_row, L.d_coo_col, L.d_coo_val, L.coo_off[p], L.coo_off[p + 1], xp, yp,
+                        h->num_sms, s);
     CK(cudaGetLastError());
     return SPG_OK;
 }

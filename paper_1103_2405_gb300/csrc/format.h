@@ -49,6 +49,9 @@ struct BuildParams {
     // 0: workloads of a part stored (and claimed) longest first by
     // latency_rounds(); 1: in the ranking order
     int claim_order = 0;
+    // also store every part as a row-sorted COO list (the TILE-COO format,
+    // the ablation of the composite storage)
+    bool build_coo = false;
 };
 
 // Dependent global-memory round trips of the warp that computes workload d
@@ -96,6 +99,11 @@ struct Layout {
     std::vector<SplitRow> split;
     std::vector<int32_t> slot_owner;
     std::vector<int64_t> edge_slot;     // edge id -> slab slot (track_edges)
+    // TILE-COO (build_coo): part p's entries are [coo_off[p], coo_off[p+1])
+    // of (row, column, value), sorted by row, then column
+    std::vector<int64_t> coo_off;
+    std::vector<int32_t> coo_row, coo_col;
+    std::vector<float> coo_val;
     // device copies
     int32_t *d_perm = nullptr, *d_inv = nullptr;
     Workload *d_wl = nullptr;
@@ -109,6 +117,8 @@ struct Layout {
     float *d_partial = nullptr;
     uint32_t *d_counter = nullptr;
     int64_t *d_edge_slot = nullptr;
+    int32_t *d_coo_row = nullptr, *d_coo_col = nullptr;
+    float *d_coo_val = nullptr;
     int64_t device_bytes = 0;
     bool on_device = false;
 

@@ -1891,6 +1891,81 @@ void launch_onehot_rows(int64_t n, int k, const int32_t *seeds, float *X, cudaSt
     count_launches(1);
 }
 
+// ------------------------------------------------------------- TILE-COO --
+//
+// The paper's TILE-COO kernel (Section 5: the tiled SpMV with COO storage,
+// against which the composite storage is measured): the entries of one part
+// as a (row, column, value) list sorted by row.  Warp w takes the intervals
+// [a, a + kCooSpan) of the list (grid stride) in 32-entry coalesced steps.
+// A step forms its 32 products, adds the segment left open by the step
+// before to its first lane when the row continues, and runs an inclusive
+// segmented scan over equal rows (rows are sorted, so equal neighbours form
+// one segment).  A lane that ends a segment inside the step adds its sum to
+// y; the last lane's segment stays open.  Only the first and the last row of
+// an interval can continue into a neighbouring interval: those are added
+// with atomicAdd, every other row with a plain read-add-write (its entries
+// of this part lie in this interval alone, and parts run one after another).
+constexpr int kCooSpan = 256;
+
+__global__ void __launch_bounds__(256)
+k_tile_coo(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
+           const float *__restrict__ val, int64_t e0, int64_t e1,
+           const float *__restrict__ x, float *__restrict__ y)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = e0 + warp * kCooSpan; a < e1; a += nwarp * kCooSpan) {
+        const int64_t b = min(a + (int64_t)kCooSpan, e1);
+        const int first = __ldg(row + a);
+        int crow = -1;       // row of the open segment (-1: none)
+        float cval = 0.f;
+        for (int64_t s = a; s < b; s += 32) {
+            const int64_t e = s + lane;
+            int r = -1;
+            float v = 0.f;
+            if (e < b) {
+                r = __ldg(row + e);
+                v = __ldg(val + e) * __ldg(x + __ldg(col + e));
+            }
+            const int r0 = __shfl_sync(kFull, r, 0);
+            if (crow >= 0 && crow != r0) {      // the open segment ended with the last step
+                if (lane == 0) {
+                    if (crow == first) atomicAdd(y + crow, cval);
+                    else y[crow] += cval;
+                }
+                crow = -1;
+            }
+            if (lane == 0 && crow >= 0) v += cval;
+            for (int d = 1; d < 32; d <<= 1) {
+                const float o = __shfl_up_sync(kFull, v, d);
+                const int ro = __shfl_up_sync(kFull, r, d);
+                if (lane >= d && ro == r) v += o;
+            }
+            const int rn = __shfl_down_sync(kFull, r, 1);
+            if (lane < 31 && rn != r && r >= 0) {
+                if (r == first) atomicAdd(y + r, v);
+                else y[r] += v;
+            }
+            crow = __shfl_sync(kFull, r, 31);
+            cval = __shfl_sync(kFull, v, 31);
+        }
+        if (lane == 0 && crow >= 0) atomicAdd(y + crow, cval);
+    }
+}
+
+void launch_tile_coo(const int32_t *row, const int32_t *col, const float *val, int64_t e0,
+                     int64_t e1, const float *x, float *y, int num_sms, cudaStream_t s)
+{
+    if (e1 <= e0) return;
+    const int64_t spans = (e1 - e0 + kCooSpan - 1) / kCooSpan;
+    int64_t blocks = (spans + 7) / 8;                    // one interval per warp
+    const int64_t cap = (int64_t)(num_sms > 0 ? num_sms : 1) * 8;   // 64 warps per SM, grid stride
+    if (blocks > cap) blocks = cap;
+    k_tile_coo<<<(int)blocks, 256, 0, s>>>(row, col, val, e0, e1, x, y);
+    count_launches(1);
+}
+
 // ------------------------------------------------------------ baselines --
 
 template <int MODE>

@@ -92,6 +92,11 @@ void launch_scatter_state(int64_t n, const int32_t *inv, const IterState *st, fl
 void launch_fill(int64_t n, float v, float *p, cudaStream_t s);
 void launch_onehot_rows(int64_t n, int k, const int32_t *seeds, float *X, cudaStream_t s);
 
+// TILE-COO SpMV over entries [e0, e1) of a row-sorted (row, column, value)
+// list: y[row] += val * x[col] (y zeroed by the caller before the first part).
+void launch_tile_coo(const int32_t *row, const int32_t *col, const float *val, int64_t e0,
+                     int64_t e1, const float *x, float *y, int num_sms, cudaStream_t s);
+
 // Plain CSR baselines on M in original order.  mode EPI_RAW or EPI_PAGERANK
 // (dangling flags per row; reductions into red[blockIdx]).
 void launch_csr_scalar(int mode, int64_t n, const int64_t *rp, const int32_t *col,

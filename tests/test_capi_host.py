@@ -279,3 +279,17 @@ def test_claim_order_puts_the_longest_latency_chain_first(spg):
         first[order] = int(r[0])
     assert first[1] in range(4)          # ranking order: a row of length 64
     assert first[0] in range(4, 68)      # longest first: a 32-row workload of 2-entry rows
+
+
+def test_tile_coo_option_builds_on_the_host(spg):
+    # the TILE-COO list is an addition: the composite format is unchanged,
+    # and a host-only handle refuses the GPU call
+    rp, col = graphgen.rmat(11, 8, seed=2)
+    a = spg.Format(rp, col, kind="pagerank", host_only=True, max_warps=200, tile_width=512)
+    b = spg.Format(rp, col, kind="pagerank", host_only=True, max_warps=200, tile_width=512, tile_coo=True)
+    for k in ("n", "nnz", "ntile", "nworkloads", "padded_slots", "zero_rows"):
+        assert a.info()[k] == b.info()[k]
+    n = rp.shape[0] - 1
+    x = np.zeros(n, np.float32)
+    with pytest.raises(spg.SpgError):
+        b.spmv_tile_coo(x, np.zeros(n, np.float32))

@@ -122,6 +122,35 @@ def test_spmv_host_pointers_and_permuted_entry():
     assert np.array_equal(yp.cpu().numpy()[pi], y)
 
 
+@pytest.mark.parametrize("gkind,opts", [("rmat14", dict()), ("rmat14", dict(tile_width=2048)),
+                                         ("rmat12", dict(tile_width=100)), ("hub", dict()),
+                                         ("varied", dict(tile_width=512)), ("dense", dict(tile_width=64)),
+                                         ("empty", dict()), ("single", dict())])
+def test_tile_coo_spmv_matches_oracle(gkind, opts):
+    # the TILE-COO ablation (Section 5): same degree order and tiles, COO
+    # storage, segmented warp sums with atomics at interval edges
+    rp, col = _graph(gkind)
+    n = rp.shape[0] - 1
+    M = oracle.build_M(rp, col)
+    f = spg.Format(rp, col, kind="pagerank", tile_coo=True, **opts)
+    x = graphgen.uniform(n, 2)
+    pi, inv = f.perm()
+    xp = torch.from_numpy(x[inv]).to(DEV)
+    yp = torch.full((n,), float("nan"), device=DEV)     # zeroed by the call
+    f.spmv_tile_coo(xp, yp)
+    torch.cuda.synchronize()
+    _check(yp.cpu().numpy()[pi], oracle.spmv(M, x), M, x)
+
+
+def test_tile_coo_needs_the_option():
+    rp, col = _graph("rmat12")
+    n = rp.shape[0] - 1
+    f = spg.Format(rp, col, kind="pagerank")
+    xp = torch.zeros(n, device=DEV)
+    with pytest.raises(spg.SpgError):
+        f.spmv_tile_coo(xp, torch.empty(n, device=DEV))
+
+
 def test_spmv_deterministic():
     rp, col = _graph("hub")
     f = spg.Format(rp, col, kind="pagerank", heavy_row=64)
