@@ -547,6 +547,9 @@ def main():
                 "kernel": "k_part_staged<EPI_PAGERANK> (fused PageRank SpMV, one launch per part)",
                 "kernel_ms": k_ms,
                 "alg_bytes_per_launch": alg_bytes,
+                # the gather upper bound: every entry's x read from DRAM
+                # (4 bytes per entry instead of x once)
+                "gather_upper_bound_gbs": (alg_bytes - 4 * n + 4 * nnz) / (k_ms * 1e-3) / 1e9,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800"}
 
     # ---- baselines on the same GPU: plain CSR-scalar and CSR-vector PageRank
