@@ -167,7 +167,7 @@ def batch_graphs(count=512):
 # the kernel source's code (kernel_source_sha) the counters were taken on:
 # reported only while that code is unchanged (null otherwise).
 NCU_TRAFFIC = {
-    "rmat22": (572_968_960, "978b3e6b76aa4dc66874e552f27821984f13ac905977169e2d629c701f50fca3"),
+    "rmat22": (572_968_960, "d5bc1293034c72376cf49e2ec72f8cca1184170f566120643e1c1d2d8faafd25"),
 }
 
 
