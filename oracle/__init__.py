@@ -64,6 +64,7 @@ def _load():
                 "orc_partition_tile": ([i64, P, P, i64, i64, i64, i32, i32, P, P, P, P, P, P,
                                         P, P, P, P, i64], i64),
                 "orc_tune_heavy": ([i64, P, P, i64, i32, i32, P, dbl, P, i64], i64),
+                "orc_split_cost_chunks": ([i64, P, i64], dbl),
                 "orc_bitonic_partition": ([i64, P, i32, P], None),
             }
             for name, (args, res) in sig.items():
@@ -284,6 +285,12 @@ def tune_heavy(row_id, row_len, max_warps, rule, table, split_cost, max_rows=0):
                                int(rule), int(nlog), _p(_c(perf, np.float64)), float(split_cost),
                                ctypes.byref(wl), int(max_rows))
     return int(H), int(wl.value)
+
+
+def split_cost_chunks(row_len, H):
+    """Chunks of the rows longer than H (the count the split cost multiplies)."""
+    rl = _c(row_len, np.int64)
+    return float(_load().orc_split_cost_chunks(rl.shape[0], _p(rl), int(H)))
 
 
 def plan_format(a_rowptr, a_col, tile_width, max_warps, table, heavy=-1, wl=0, rule=1,

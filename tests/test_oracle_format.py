@@ -211,3 +211,119 @@ def test_rule1_tie_goes_to_column_major(w, h):
                                      table=_const_table())
         assert list(part["wl_h"]) == [h] and list(part["wl_w"]) == [w]
         assert list(part["wl_major"]) == [major]
+
+
+# ---- the row cap (at most max_rows rows per workload, GB300 reading of the
+# packing step) and the per-chunk split cost of the heavy-row tuning, pinned
+# by cases worked out by hand below (not by the builder)
+
+def _cap_case():
+    # 40 rows of 64 entries, then 70 rows of 1 entry; WL = 2560 = 40 * 64
+    return np.array([64] * 40 + [1] * 70, np.int64)
+
+
+def test_row_cap_packing_hand_computed():
+    rl = _cap_case()
+    ids = np.arange(rl.size, dtype=np.int64)
+    # cap 32 (rule 1):
+    #   rank 0:  w = 64, h = min(2560/64 = 40, 32) = 32: row-major 32 * 64 =
+    #            2048 slots, column-major 32 * 64 = 2048 -> tie -> column-major
+    #   rank 32: w = 64 (rows 32..39 have 64 entries), h = 32 -> column-major
+    #   rank 64: w = 1,  h = min(2560, 32, 46 left) = 32 -> column-major
+    #   rank 96: w = 1,  h = 14 (the rows left) -> column-major
+    capped = oracle.partition_tile(ids, rl, heavy=0, wl=2560, max_warps=1000, rule=1,
+                                   table=_const_table(), max_rows=32)
+    assert list(capped["wl_first"]) == [0, 32, 64, 96]
+    assert list(capped["wl_h"]) == [32, 32, 32, 14]
+    assert list(capped["wl_w"]) == [64, 64, 1, 1]
+    assert list(capped["wl_major"]) == [1, 1, 1, 1]
+    # no cap: rank 0 takes all 40 rows of 64 (row-major 40 * 64 = 2560 <
+    # column-major 64 * 64 = 4096), rank 40 the 70 one-entry rows
+    # (column-major, h padded to 96)
+    free = oracle.partition_tile(ids, rl, heavy=0, wl=2560, max_warps=1000, rule=1,
+                                 table=_const_table(), max_rows=0)
+    assert list(free["wl_first"]) == [0, 40]
+    assert list(free["wl_h"]) == [40, 70]
+    assert list(free["wl_major"]) == [0, 1]
+
+
+def test_row_cap_model_hand_computed():
+    rl = _cap_case()
+    # padded sizes with the cap: 64 * 32 + 64 * 32 + 1 * 32 + 1 * 32 = 4160
+    # slots, all column-major; without it: 64 * 40 (row-major) + 1 * 96
+    # (column-major) = 2656
+    assert oracle.alg3_model(rl, 2560, 1000, 1, _const_table(1.0), max_rows=32) == 4160.0
+    assert oracle.alg3_model(rl, 2560, 1000, 1, _const_table(1.0), max_rows=0) == 2656.0
+    # row-major table 2, column-major 1, one warp per iteration (Eq. 1):
+    # capped: four column-major iterations, 2048 + 2048 + 32 + 32 = 4160;
+    # uncapped: 2560 / 2 + 96 / 1 = 1376
+    t = _major_table(2.0, 1.0)
+    assert abs(oracle.alg3_model(rl, 2560, 1, 1, t, max_rows=32) - 4160.0) < 1e-9
+    assert abs(oracle.alg3_model(rl, 2560, 1, 1, t, max_rows=0) - 1376.0) < 1e-9
+    # two warps per iteration, table by column-major height bucket: h_pad 32
+    # (log2 5) runs at 4, everything else at 1 -> capped iterations
+    # {2048, 2048} at P = 4 and {32, 32} at P = 4: 1024 + 16 = 1040
+    nlog = 21
+    perf = np.ones(2 * nlog * nlog)
+    for lw in range(nlog):
+        perf[(1 * nlog + lw) * nlog + 5] = 4.0
+    assert abs(oracle.alg3_model(rl, 2560, 2, 1, (nlog, perf), max_rows=32) - 1040.0) < 1e-9
+    # the cap bounds rows, not WL: a cap of 40 leaves this plan as uncapped
+    assert oracle.alg3_model(rl, 2560, 1000, 1, _const_table(1.0), max_rows=40) == 2656.0
+
+
+def test_row_cap_one_entry_rows():
+    # 100 one-entry rows, cap 32: workloads of 32, 32, 32 and 4 rows, each
+    # a 1 x 32 column-major rectangle (128 padded slots in all)
+    rl = np.ones(100, np.int64)
+    part = oracle.partition_tile(np.arange(100, dtype=np.int64), rl, heavy=0, wl=1000,
+                                 max_warps=1000, rule=1, table=_const_table(), max_rows=32)
+    assert list(part["wl_h"]) == [32, 32, 32, 4]
+    assert list(part["wl_major"]) == [1, 1, 1, 1]
+    assert oracle.alg3_model(rl, 1000, 1000, 1, _const_table(1.0), max_rows=32) == 128.0
+    # by height bucket: h_pad 32 at 2 and h_pad 128 (log2 7) at 1: capped
+    # 128 / 2 = 64, uncapped one 1 x 128 rectangle 128 / 1 = 128
+    nlog = 21
+    perf = np.ones(2 * nlog * nlog)
+    perf[(1 * nlog + 0) * nlog + 5] = 2.0
+    assert abs(oracle.alg3_model(rl, 1000, 1000, 1, (nlog, perf), max_rows=32) - 64.0) < 1e-12
+    assert abs(oracle.alg3_model(rl, 1000, 1000, 1, (nlog, perf), max_rows=0) - 128.0) < 1e-12
+
+
+def _split_table():
+    # every shape at 1 except row-major rectangles 64..127 slots wide (w_pad
+    # 128 -> log2 7), which run at 0.5
+    nlog = 21
+    perf = np.ones(2 * nlog * nlog)
+    for lh in range(nlog):
+        perf[(0 * nlog + 7) * nlog + lh] = 0.5
+    return nlog, perf
+
+
+@pytest.mark.parametrize("split_cost,H,wl", [(0.0, 64, 64), (10.0, 64, 64), (42.0, 64, 64),
+                                             (43.0, 128, 128), (50.0, 128, 128)])
+def test_tune_heavy_split_cost_hand_computed(split_cost, H, wl):
+    # One row of 128 entries and four of 32; nnz = 256, max_warps = 2:
+    # base = 128, candidates H = 128, 64, 32 (k = 3 gives 32 again, skipped).
+    #   H = 128: no split; Algorithm 2 range WL in {128}: workloads 128 x 1
+    #            (row-major, w_pad 128 -> 0.5) and 32 x 4 (1) in one
+    #            iteration: 256 / 0.75 = 341.33; no chunk
+    #   H = 64:  virtual rows 64, 64, 32 x 4; WL in {64, 128} both model 256
+    #            (every rectangle at 1), the first is kept: WL = 64; 2 chunks
+    #   H = 32:  eight 32-entry virtual rows, model 256 for every WL; 4 chunks
+    # cost = model + split_cost * chunks: H = 64 wins while
+    # 256 + 2 s < 341.33, i.e. s < 42.67; above that H = 128 (cost 341.33)
+    rl = np.array([128, 32, 32, 32, 32], np.int64)
+    ids = np.arange(5, dtype=np.int64)
+    got = oracle.tune_heavy(ids, rl, 2, 1, _split_table(), split_cost=split_cost)
+    assert got == (H, wl)
+    # the same with the row cap on (no workload here exceeds 32 rows)
+    assert oracle.tune_heavy(ids, rl, 2, 1, _split_table(), split_cost, max_rows=32) == (H, wl)
+
+
+def test_split_chunk_count_hand_computed():
+    rl = np.array([128, 32, 32, 32, 32, 0, 65], np.int64)
+    # rows longer than H are counted by their chunks, the others not at all
+    assert oracle.split_cost_chunks(rl, 128) == 0.0
+    assert oracle.split_cost_chunks(rl, 64) == 2.0 + 2.0      # 128 -> 2, 65 -> 2
+    assert oracle.split_cost_chunks(rl, 32) == 4.0 + 3.0      # 128 -> 4, 65 -> 3
