@@ -449,9 +449,11 @@ spg_status spg_baseline_pagerank(spg_handle h, spg_baseline which, float damping
  * where a cudaMalloc can fail or stall the device.  This call allocates
  * nothing (no cudaMalloc, no cudaFree, no allocating library routine):
  * the scratch its kernels need -- partial sums and arrival counters of rows
- * cut into chunks, work counters of the shared-memory kernel -- lives in one
+ * cut into chunks, work counters of the persistent kernels -- lives in one
  * fixed array of 1,311,744 bytes inside the library, which every GPU that
- * loads the library holds until the process exits.
+ * loads the library holds until the process exits.  It runs the kernel
+ * option the handle was built with (spg_build_opts.kernel), as
+ * spg_spmv_permuted does.
  *
  *  - Limits: formats with at most 128 parts, 65,536 split rows and 262,144
  *    split chunks (spg_format_info: ntile + 1, split_rows, split_chunks);
@@ -459,6 +461,10 @@ spg_status spg_baseline_pagerank(spg_handle h, spg_baseline which, float damping
  *  - The handle's device must be the current device.  The first call on a
  *    device looks up the array's device address (cudaGetSymbolAddress) with
  *    that device current; make that first call before any stream capture.
+ *    The address is kept for the life of the process: resetting the device
+ *    (cudaDeviceReset) after that first call is not supported.
+ *  - x_perm and y_perm need the alignment of a float (4 bytes); the kernels
+ *    use 16-byte loads of x only where the address allows them.
  *  - Every call on a device shares the one array and it keeps the last
  *    call's contents: the call clears its counters on `stream` before its
  *    kernels, but calls whose work overlaps on the GPU (other streams,

@@ -717,48 +717,70 @@ extern "C" spg_status spg_format_export_entries(spg_handle h, int64_t *orows, in
 // shared memory, one block per SM; the rest (and every part when staging is
 // off) get 8-warp blocks, one warp per workload.  Block reduction slots are
 // laid out part after part; split rows reduce after all blocks.
+// Launch view of part p of layout L (everything but the reduction base).
+// `staged` selects the handle's persistent kernel option; `sched` is the
+// part's pair of work counters (nullptr when the kernel takes none).
+static PartView part_view(spg_handle h, const Layout &L, size_t p, bool staged, uint32_t *sched)
+{
+    const PartHost &ph = L.parts[p];
+    PartView pv;
+    std::memset(&pv, 0, sizeof pv);
+    pv.wl = L.d_wl + ph.wl_off;
+    pv.rows = L.d_rows;
+    pv.slab = L.d_slab;
+    pv.slab4 = L.d_slab4;
+    pv.sched = sched;
+    pv.nwl = (int32_t)ph.nwl_total;
+    pv.c0 = (int32_t)ph.c0;
+    pv.pf_ahead = h->pf_ahead;
+    pv.status = h->d_status;
+    const int64_t width = ph.c1 - ph.c0;
+    if (staged && h->kernel == 4 && ph.nwl_total > 0) {
+        // persistent 8-warp blocks, several per SM, no x slice
+        pv.persist = 1;
+        pv.xs_cols = 0;
+        pv.nblocks = (int32_t)std::min<int64_t>((int64_t)h->num_sms * h->persist_blocks,
+                                                (ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    } else if (staged && h->kernel == 3 && !L.pattern && ph.nwl_total > 0) {
+        // TMA-pipelined persistent kernel (x slice when the part is wide enough)
+        pv.tma = 1;
+        pv.xs_cols = width >= 1024 ? (int32_t)std::min<int64_t>(kTmaMaxCols, width) : 0;
+        pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
+    } else if (staged && width >= 1024 && ph.nwl_total > 0) {
+        pv.xs_cols = (int32_t)std::min<int64_t>(h->stage_cols, width);
+        pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
+    } else {
+        pv.xs_cols = 0;
+        pv.nblocks = (int32_t)((ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    }
+    pv.units = L.d_units + ph.unit_off;
+    pv.nunits = (int32_t)ph.nunits;
+    return pv;
+}
+
+// Whether the handle's persistent kernel option applies (it needs work
+// counters; option 2 is the plain one-warp-per-workload kernel).
+static bool staged_option(spg_handle h, bool want, bool have_sched)
+{
+    return want && (h->stage_cols > 0 || h->kernel >= 3) && h->kernel != 2 && have_sched;
+}
+
+// Launch views of the forward layout.  Staged: the handle's persistent
+// kernel option (default: persistent 8-warp blocks; option 1: parts at least
+// 1024 columns wide get one block per SM with min(stage_cols, width) columns
+// of x in shared memory); the rest (and every part when staging is off) get
+// 8-warp blocks, one warp per workload.  Block reduction slots are laid out
+// part after part; split rows reduce after all blocks.
 static spg_format_t::Views &get_views_L(spg_handle h, const Layout &L,
                                         spg_format_t::LayoutRT &rt, bool staged)
 {
-    staged = staged && (h->stage_cols > 0 || h->kernel >= 3) && h->kernel != 2 && rt.sched.p;
+    staged = staged_option(h, staged, rt.sched.p != nullptr);
     spg_format_t::Views &V = staged ? rt.vstaged : rt.vplain;
     if (V.built) return V;
     int32_t base = 0;
     V.v.clear();
     for (size_t p = 0; p < L.parts.size(); ++p) {
-        const PartHost &ph = L.parts[p];
-        PartView pv;
-        std::memset(&pv, 0, sizeof pv);
-        pv.wl = L.d_wl + ph.wl_off;
-        pv.rows = L.d_rows;
-        pv.slab = L.d_slab;
-        pv.slab4 = L.d_slab4;
-        pv.sched = rt.sched.p ? rt.sched.p + 2 * p : nullptr;
-        pv.nwl = (int32_t)ph.nwl_total;
-        pv.c0 = (int32_t)ph.c0;
-        pv.pf_ahead = h->pf_ahead;
-        pv.status = h->d_status;
-        const int64_t width = ph.c1 - ph.c0;
-        if (staged && h->kernel == 4 && ph.nwl_total > 0) {
-            // persistent 8-warp blocks, several per SM, no x slice
-            pv.persist = 1;
-            pv.xs_cols = 0;
-            pv.nblocks = (int32_t)std::min<int64_t>((int64_t)h->num_sms * h->persist_blocks,
-                                                    (ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
-        } else if (staged && h->kernel == 3 && !L.pattern && ph.nwl_total > 0) {
-            // TMA-pipelined persistent kernel (x slice when the part is wide enough)
-            pv.tma = 1;
-            pv.xs_cols = width >= 1024 ? (int32_t)std::min<int64_t>(kTmaMaxCols, width) : 0;
-            pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
-        } else if (staged && width >= 1024 && ph.nwl_total > 0) {
-            pv.xs_cols = (int32_t)std::min<int64_t>(h->stage_cols, width);
-            pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
-        } else {
-            pv.xs_cols = 0;
-            pv.nblocks = (int32_t)((ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
-        }
-        pv.units = L.d_units + ph.unit_off;
-        pv.nunits = (int32_t)ph.nunits;
+        PartView pv = part_view(h, L, p, staged, rt.sched.p ? rt.sched.p + 2 * p : nullptr);
         pv.red_base = base;
         base += pv.nblocks;
         V.v.push_back(pv);
@@ -1448,8 +1470,8 @@ extern "C" spg_status spg_time_parts(spg_handle h, int mode, int reps, float *ms
 // spg_spmv_permuted_noalloc runs the same tiled-composite SpMV launches as
 // spg_spmv_permuted, but every piece of scratch those kernels need -- the
 // partial sums and arrival counters of rows cut into chunks, and the work
-// counters of the persistent shared-memory kernel -- comes from the fixed
-// array below instead of from device memory the handle allocated.  The
+// counters of the persistent kernels -- comes from the fixed array below
+// instead of from device memory the handle allocated.  The
 // array is part of the library image: every GPU that loads the library
 // holds it (kNoAllocBytes) until the process exits.
 
@@ -1514,28 +1536,10 @@ extern "C" spg_status spg_spmv_permuted_noalloc(spg_handle h, const float *x_per
     SplitView sv = L.split_view();
     sv.partial = partial;
     sv.counter = counter;
+    // the handle's own kernel option, with this call's counters in the array
+    const bool staged = staged_option(h, true, true);
     for (size_t p = 0; p < L.parts.size(); ++p) {
-        const PartHost &ph = L.parts[p];
-        PartView pv;
-        std::memset(&pv, 0, sizeof pv);
-        pv.wl = L.d_wl + ph.wl_off;
-        pv.rows = L.d_rows;
-        pv.slab = L.d_slab;
-        pv.slab4 = L.d_slab4;
-        pv.units = L.d_units + ph.unit_off;
-        pv.nunits = (int32_t)ph.nunits;
-        pv.sched = sched + 2 * p;
-        pv.nwl = (int32_t)ph.nwl_total;
-        pv.c0 = (int32_t)ph.c0;
-        pv.pf_ahead = h->pf_ahead;
-        const int64_t width = ph.c1 - ph.c0;
-        if (h->stage_cols > 0 && width >= 1024 && ph.nwl_total > 0) {
-            pv.xs_cols = (int32_t)std::min<int64_t>(h->stage_cols, width);
-            pv.nblocks = (int32_t)std::min<int64_t>(h->num_sms, (ph.nwl_total + 31) / 32);
-        } else {
-            pv.xs_cols = 0;
-            pv.nblocks = (int32_t)((ph.nwl_total + kWarpsPerBlock - 1) / kWarpsPerBlock);
-        }
+        const PartView pv = part_view(h, L, p, staged, sched + 2 * p);
         launch_part(EPI_RAW, pv, sv, x_perm, y_perm, nullptr, nullptr, s);
     }
     CK(cudaGetLastError());

@@ -639,7 +639,9 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
     constexpr bool kStage = NT == kStagedBlock;
     const int S = kStage ? pv.xs_cols : 0, c0 = pv.c0;
     if (kStage) {
-        if (((c0 | S) & 3) == 0) {
+        // 16-byte copies only where the caller's x address allows them (x
+        // may be any float-aligned device pointer, e.g. a tensor slice)
+        if (((c0 | S) & 3) == 0 && (reinterpret_cast<uintptr_t>(gsrc + c0) & 15) == 0) {
             const float4 *src = reinterpret_cast<const float4 *>(gsrc + c0);
             float4 *dst = reinterpret_cast<float4 *>(xs);
             for (int i = threadIdx.x; i < (S >> 2); i += blockDim.x) dst[i] = __ldg(src + i);
@@ -838,7 +840,7 @@ k_part_tma(PartView pv, SplitView sv, const float *__restrict__ xin, float *__re
     resolve_xy<MODE>(st, x, y);
     if (MODE == EPI_ADJ) E.xs = x[E.seed];
     const int S = pv.xs_cols, c0 = pv.c0;
-    if (((c0 | S) & 3) == 0) {
+    if (((c0 | S) & 3) == 0 && (reinterpret_cast<uintptr_t>(x + c0) & 15) == 0) {
         const float4 *src4 = reinterpret_cast<const float4 *>(x + c0);
         float4 *dst4 = reinterpret_cast<float4 *>(xs);
         for (int i = threadIdx.x; i < (S >> 2); i += blockDim.x) dst4[i] = __ldg(src4 + i);

@@ -33,7 +33,8 @@ def _close(y, ref):
     assert np.allclose(y, ref, rtol=1e-5, atol=1e-7)
 
 
-@pytest.mark.parametrize("opts", [dict(tile_width=2048, heavy_row=64), dict(x_stage_cols=-1)])
+@pytest.mark.parametrize("opts", [dict(tile_width=2048, heavy_row=64), dict(x_stage_cols=-1),
+                                  dict(tile_width=2048, heavy_row=64, kernel=1)])
 def test_noalloc_matches_allocating_entry_point_twice(opts):
     rp, col = graphgen.rmat(14, 8, seed=1)
     f = spg.Format(rp, col, kind="pagerank", **opts)
@@ -71,3 +72,45 @@ def test_noalloc_refuses_formats_beyond_its_limits():
     yp = torch.empty(f.n, device=DEV)
     assert _call_noalloc(f, xp, yp) == -1
     assert b"split rows" in spg.lib().spg_last_error()
+
+
+def test_noalloc_allocates_no_device_memory():
+    # after a first call (which looks up the array's address and loads the
+    # kernels), further calls leave the device's free memory unchanged
+    rp, col = graphgen.rmat(14, 8, seed=1)
+    f = spg.Format(rp, col, kind="pagerank", tile_width=2048, heavy_row=64)
+    xp = torch.from_numpy(graphgen.uniform(f.n, 2)).to(DEV)
+    y = torch.empty(f.n, device=DEV)
+    assert _call_noalloc(f, xp, y) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(DEV)
+    for _ in range(3):
+        assert _call_noalloc(f, xp, y) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(DEV)
+    assert free1 == free0
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_noalloc_and_permuted_accept_an_unaligned_x_view(kernel):
+    # x' as a slice one float into a buffer (4-byte aligned, not 16): the
+    # shared-memory x slice must not use 16-byte loads there
+    import oracle
+    rp, col = graphgen.rmat(14, 8, seed=1)
+    f = spg.Format(rp, col, kind="pagerank", tile_width=2048, kernel=kernel)
+    n = f.n
+    pi, inv = f.perm()
+    x = graphgen.uniform(n, 2)
+    big = torch.zeros(n + 1, device=DEV)
+    big[1:] = torch.from_numpy(x[inv]).to(DEV)
+    xp = big[1:]
+    assert xp.data_ptr() % 16 != 0
+    ref = oracle.spmv(oracle.build_M(rp, col), x)[inv]
+    y1 = torch.empty(n, device=DEV)
+    f.spmv_permuted(xp, y1)
+    y2 = torch.empty(n, device=DEV)
+    assert _call_noalloc(f, xp, y2) == 0
+    torch.cuda.synchronize()
+    for y in (y1, y2):
+        y = y.double().cpu().numpy()
+        assert np.linalg.norm(y - ref) <= 1e-5 * np.linalg.norm(ref)
