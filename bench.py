@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="spg", choices=["spg", "reference"])
-    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat26", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--host-loop", action="store_true",
                     help="iterate with direct launches (host loop) instead of the CUDA-graph "
@@ -97,12 +97,13 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="spg_clocks_", suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
@@ -125,7 +126,13 @@ class Clocks:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) >= 9:
                 try:
@@ -437,9 +444,34 @@ def run_unstructured(args):
     emit(args, "SpMV GFLOP/s (2*nnz)", 2.0 * nnz / (ms * 1e-3) / 1e9, "GFLOP/s", ms, cfg, extra)
 
 
-def cpu_leg(rp, col, nnz, budget_s=12.0, max_iters=40):
+def host_cpu():
+    """Core count and CPU model string of the host running the oracle."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "arch": platform.machine()}
+
+
+def cpu_leg(rp, col, nnz, budget_s=20.0, max_iters=40):
     """The FP64 oracle (as it stands, 1 thread) on a bounded sample: as many
-    PageRank iterations of the same graph as fit in ~budget_s."""
+    PageRank iterations of the same graph as fit in ~budget_s (one
+    calibration iteration first, untimed)."""
     import oracle
     M = oracle.build_M(rp, col)
     t0 = time.perf_counter()
@@ -451,7 +483,7 @@ def cpu_leg(rp, col, nnz, budget_s=12.0, max_iters=40):
     t = time.perf_counter() - t0
     return {"value": 2.0 * nnz * iters / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
             "sample": f"{iters} FP64 PageRank iterations (Eq. 6) of the full graph, single thread",
-            "seconds": t}
+            "seconds": t, "host": host_cpu()}
 
 
 def run_reference(args):
@@ -466,20 +498,28 @@ def run_reference(args):
     nnz = int(rp[-1])
     import oracle
     M = oracle.build_M(rp, col)
-    for _ in range(args.warmup):
-        oracle.pagerank(rp, col, DAMPING, tol=0.0, max_iter=1, M=M)
+    # bounded sample: warm-up iterations (at most 2, the first one timed to
+    # size the sample), then as many of the K steps as fit in about 45 s of
+    # single-thread CPU time (a billion-edge iteration takes several seconds)
+    warm = max(1, min(args.warmup, 2))
     t0 = time.perf_counter()
-    oracle.pagerank(rp, col, DAMPING, tol=0.0, max_iter=args.steps, M=M)
+    for _ in range(warm):
+        oracle.pagerank(rp, col, DAMPING, tol=0.0, max_iter=1, M=M)
+    one = (time.perf_counter() - t0) / warm
+    steps = int(max(1, min(args.steps, 45.0 / max(one, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.pagerank(rp, col, DAMPING, tol=0.0, max_iter=steps, M=M)
     t = time.perf_counter() - t0
-    v = 2.0 * nnz * args.steps / t / 1e9
+    v = 2.0 * nnz * steps / t / 1e9
     line = {"impl": "reference", "metric": "SpMV GFLOP/s (2*nnz) in PageRank iterations",
-            "value": v, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "value": v, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": steps,
+            "warmup": warm, "ms_per_step": 1e3 * t / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "n": int(rp.shape[0] - 1),
                        "nnz": nnz},
             "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} FP64 PageRank iterations, single thread"},
+                             "sample": f"{steps} FP64 PageRank iterations, single thread",
+                             "host": host_cpu()},
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

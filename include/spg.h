@@ -99,9 +99,14 @@ typedef struct {
     /* Storage rule of a workload: 0 = the paper's (row-major iff w >= h),
      * 1 = the major with fewer padded slots (column-major on a tie: its 32
      * rows proceed side by side, where a row-major warp walks them one
-     * after another; default),
+     * after another),
      * 2 = every workload row-major (the CSR-vector special case), 3 = every
-     * workload column-major (the ELL special case; Section 5). */
+     * workload column-major (the ELL special case; Section 5),
+     * 4 = automatic (the default when opts is NULL): per part, the rule of
+     * 0-3 whose plan -- its own split threshold and Algorithm 2 workload
+     * size -- the Algorithm 3 model prices lowest (first of 1, 0, 2, 3 on a
+     * tie); spg_tile_info reports the rule each part got.  A zeroed
+     * options struct selects rule 0: set 4 for the automatic choice. */
     int layout_rule;
     /* Maximum resident warps of the whole GPU used by Algorithms 2-3.
      * 0 = query the current device (SMs x resident warps of the kernel). */
@@ -242,6 +247,7 @@ typedef struct {
     int64_t nwl;                /* workloads, zero-row workloads excluded */
     int64_t nnz;                /* non-zeros in the part */
     double predicted_ms;
+    int64_t layout_rule;        /* storage rule the part was built with (0-3) */
 } spg_tile_info_t;
 
 /* ---------------------------------------------------------------- build -- */

@@ -293,6 +293,37 @@ def split_cost_chunks(row_len, H):
     return float(_load().orc_split_cost_chunks(rl.shape[0], _p(rl), int(H)))
 
 
+AUTO_RULE = 4
+
+
+def plan_cost(row_id, row_len, heavy, wl, max_warps, rule, table, split_cost, max_rows=0):
+    """Modelled cost of one tile's plan under storage rule `rule`: split
+    threshold (tuned when heavy < 0), Algorithm 2 workload size (wl = 0) and
+    the Algorithm 3 time of that plan, plus split_cost per chunk of a split
+    row."""
+    rl = _c(row_len, np.int64)
+    if int(rl[rl > 0].sum()) == 0:
+        return 0.0
+    H = tune_heavy(row_id, rl, max_warps, rule, table, split_cost, max_rows)[0] if heavy < 0 else heavy
+    part = partition_tile(row_id, rl, H, wl, max_warps, rule, table, max_rows)
+    t = alg3_model(part["rank_len"], part["WL"], max_warps, rule, table, max_rows)
+    return t + split_cost * (split_cost_chunks(rl, H) if H > 0 else 0.0)
+
+
+def choose_rule(row_id, row_len, heavy, wl, max_warps, table, split_cost, max_rows=0):
+    """Section 5 reading: CSR-vector (rule 2) and ELL (rule 3) are special
+    cases of the composite format, as are the paper's w >= h rule (0) and
+    the fewer-padded-slots rule (1); the automatic storage rule takes, per
+    tile, the one whose plan Algorithm 3 prices lowest (first of 1, 0, 2, 3
+    on a tie)."""
+    best, best_r = np.inf, 1
+    for r in (1, 0, 2, 3):
+        c = plan_cost(row_id, row_len, heavy, wl, max_warps, r, table, split_cost, max_rows)
+        if c < best:
+            best, best_r = c, r
+    return best_r
+
+
 def plan_format(a_rowptr, a_col, tile_width, max_warps, table, heavy=-1, wl=0, rule=1,
                 split_cost=0.0, M=None, max_rows=0):
     """The tiled composite layout of M = W^T, step by step in the paper's order.
@@ -326,11 +357,14 @@ def plan_format(a_rowptr, a_col, tile_width, max_warps, table, heavy=-1, wl=0, r
         rl = np.bincount(rows_p[m], minlength=n).astype(np.int64)
         touched |= rl > 0
         ids = np.arange(n, dtype=np.int64)
+        r = choose_rule(ids, rl, heavy, wl, max_warps, table, split_cost, max_rows) \
+            if rule == AUTO_RULE else rule
         if heavy < 0:
-            H, _ = tune_heavy(ids, rl, max_warps, rule, table, split_cost, max_rows)
+            H, _ = tune_heavy(ids, rl, max_warps, r, table, split_cost, max_rows)
         else:
             H = heavy
-        part = partition_tile(ids, rl, H, wl, max_warps, rule, table, max_rows)
+        part = partition_tile(ids, rl, H, wl, max_warps, r, table, max_rows)
+        part["rule"] = r
         tiles.append((c0, c1, H, part))
     zero_rows = np.flatnonzero(~touched).astype(np.int64)
     return dict(pi=pi, inv=inv, ntile=ntile, tiles=tiles, zero_rows=zero_rows)

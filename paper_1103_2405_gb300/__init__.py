@@ -68,7 +68,7 @@ class _Info(ctypes.Structure):
 class _TileInfo(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in
                 ("col_begin", "col_end", "heavy", "wl", "nvirt", "nwl", "nnz")] + \
-               [("predicted_ms", ctypes.c_double)]
+               [("predicted_ms", ctypes.c_double), ("layout_rule", ctypes.c_int64)]
 
 
 # Every symbol include/spg.h declares.
@@ -202,7 +202,7 @@ class Format:
     logits (kind 'weighted').  Build options map 1:1 to spg_build_opts."""
 
     def __init__(self, rowptr, col, val=None, kind="pagerank", tile_width=0, wl=0, heavy_row=-1,
-                 layout_rule=1, max_warps=0, vec_width=1, build_transpose=False, keep_plan=False,
+                 layout_rule=4, max_warps=0, vec_width=1, build_transpose=False, keep_plan=False,
                  keep_csr=False, host_only=False, split_cost=0.0, table=None, x_stage_cols=0,
                  slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, pattern_only=False,
                  row_part=None, part_id=0, nparts=None, unit_slots=0, separate_check=False,
@@ -284,7 +284,7 @@ class Format:
         f, h, w, m = (np.empty(t["nwl"], np.int64) for _ in range(4))
         _check(lib().spg_format_export_plan(self._h, int(part), *(_ptr(a)[0] for a in
                                                                     (rr, rc, rl, f, h, w, m))))
-        return dict(WL=t["wl"], heavy=t["heavy"], rank_row=rr, rank_chunk=rc, rank_len=rl,
+        return dict(WL=t["wl"], heavy=t["heavy"], rule=t["layout_rule"], rank_row=rr, rank_chunk=rc, rank_len=rl,
                     wl_first=f, wl_h=h, wl_w=w, wl_major=m)
 
     def export_entries(self):
@@ -465,7 +465,7 @@ class BatchFormat:
     """Many independent graphs in one handle (spg_build_batch): one
     tiled-composite sweep per iteration over all of them."""
 
-    def __init__(self, graphs, heavy_row=-1, layout_rule=1, max_warps=0, x_stage_cols=0,
+    def __init__(self, graphs, heavy_row=-1, layout_rule=4, max_warps=0, x_stage_cols=0,
                  slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, host_only=False, table=None,
                  claim_order=0, stream=None):
         L = lib()

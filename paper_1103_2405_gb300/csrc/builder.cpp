@@ -339,6 +339,31 @@ static int64_t tune_heavy(const std::vector<int32_t> &len, int64_t nnz, const Bu
     return bestH;
 }
 
+// Modelled cost of one part's plan under prm.layout_rule: the split
+// threshold (tuned or given), Algorithm 2's workload size (or the given
+// one), Algorithm 3's time plus split_cost per chunk of a split row -- the
+// quantity the automatic storage rule minimises.
+static double plan_cost(const std::vector<int32_t> &len, int64_t nnz, const BuildParams &prm,
+                        const PerfTable &t, int64_t *H_out)
+{
+    const int64_t H = prm.heavy < 0 ? tune_heavy(len, nnz, prm, t) : prm.heavy;
+    *H_out = H;
+    if (nnz == 0) return 0.0;
+    std::vector<int32_t> rr, rc, rl;
+    rank_rows(len, H, rr, rc, rl);
+    const int64_t nv = (int64_t)rl.size();
+    double tm = 0.0;
+    const int64_t WL = prm.wl > 0 ? prm.wl
+                                  : alg2_search(rl.data(), nv, nnz, prm.max_warps, prm.layout_rule,
+                                                prm.max_rows, t, &tm);
+    if (prm.wl > 0) tm = model_time(rl.data(), nv, WL, prm.max_warps, prm.layout_rule, prm.max_rows, t);
+    double chunks = 0.0;
+    if (H > 0)
+        for (int32_t L : len)
+            if (L > H) chunks += (double)((L + H - 1) / H);
+    return tm + prm.split_cost * chunks;
+}
+
 // ---------------------------------------------------------------- builder --
 
 bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, std::string &err)
@@ -519,7 +544,36 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
             pn += l;
         }
         ph.nnz = pn;
-        int64_t H = prm.heavy < 0 ? tune_heavy(len, pn, prm, table) : prm.heavy;
+        // storage rule of the part: the given one, or (kAutoRule) the rule
+        // of rules 0-3 whose plan -- its own split threshold and workload
+        // size -- the Algorithm 3 model prices lowest (Section 5: CSR-vector
+        // and ELL are special cases of the composite format); ties keep the
+        // first in the order 1, 0, 2, 3
+        int rule = prm.layout_rule;
+        int64_t H = -1;
+        if (rule == kAutoRule) {
+            // the four plans priced side by side (one thread each)
+            const int order[4] = {1, 0, 2, 3};
+            double cost[4];
+            int64_t hs[4];
+            std::vector<std::thread> th;
+            for (int k = 0; k < 4; ++k)
+                th.emplace_back([&, k] {
+                    BuildParams q = prm;
+                    q.layout_rule = order[k];
+                    cost[k] = plan_cost(len, pn, q, table, &hs[k]);
+                });
+            for (auto &x : th) x.join();
+            int kb = 0;
+            for (int k = 1; k < 4; ++k)
+                if (cost[k] < cost[kb]) kb = k;
+            rule = order[kb];
+            H = hs[kb];
+        }
+        ph.rule = rule;
+        BuildParams pr = prm;
+        pr.layout_rule = rule;
+        if (H < 0) H = prm.heavy < 0 ? tune_heavy(len, pn, pr, table) : prm.heavy;
         ph.heavy = H;
         rank_rows(len, H, rank_row[p], rank_chunk[p], rank_len[p]);
         const int64_t nv = (int64_t)rank_len[p].size();
@@ -527,9 +581,9 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
         double tm = 0.0;
         int64_t WL = prm.wl > 0 ? prm.wl
                                 : alg2_search(rank_len[p].data(), nv, pn, prm.max_warps,
-                                              prm.layout_rule, prm.max_rows, table, &tm);
+                                              rule, prm.max_rows, table, &tm);
         if (prm.wl > 0)
-            tm = model_time(rank_len[p].data(), nv, WL, prm.max_warps, prm.layout_rule,
+            tm = model_time(rank_len[p].data(), nv, WL, prm.max_warps, rule,
                             prm.max_rows, table);
         ph.wl = nv > 0 ? WL : 0;
         ph.predicted_s = tm;
@@ -538,7 +592,7 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
             wfirst[p].push_back(i);
             wh[p].push_back((int32_t)h);
             ww[p].push_back((int32_t)w);
-            wm[p].push_back(pick_major(prm.layout_rule, w, h));
+            wm[p].push_back(pick_major(rule, w, h));
             i += h;
         }
         ph.nwl = (int64_t)wfirst[p].size();

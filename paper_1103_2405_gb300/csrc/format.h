@@ -25,11 +25,14 @@ void perf_table_default(PerfTable &t);  // built-in analytic table
 bool perf_table_load(const char *path, PerfTable &t, std::string &err);
 double perf_lookup(const PerfTable &t, int major, int64_t wpad, int64_t hpad);
 
+// Storage rule value that lets the Algorithm 3 model choose rule 0-3 per part.
+constexpr int kAutoRule = 4;
+
 struct BuildParams {
     int64_t tile_width = 0;   // resolved (> 0) or <= 0 for none
     int64_t wl = 0;
     int64_t heavy = -1;
-    int layout_rule = 1;
+    int layout_rule = 1;      // 0-3, or kAutoRule (chosen per part by the model)
     int64_t max_warps = 9728;
     int64_t max_rows = 0;     // > 0: at most this many rows per workload
     double split_cost = 2e-7;
@@ -65,6 +68,7 @@ double latency_rounds(const Workload &d);
 struct PartHost {
     int64_t c0 = 0, c1 = 0;
     int64_t heavy = 0, wl = 0, nnz = 0, nvirt = 0;
+    int32_t rule = 1;         // storage rule the part was built with (0-3)
     int64_t nwl = 0;          // regular workloads
     int64_t nwl_total = 0;    // + zero-row workloads
     int64_t unit_off = 0, nunits = 0;   // claim units: units[unit_off .. unit_off + nunits] (+ end)

@@ -63,6 +63,9 @@ CASES = [  # (scale, ef, tile_width, heavy, rule, max_warps, max_rows)
     (12, 8, 512, -1, 1, 40, 37),
     (12, 8, 1024, -1, 2, 300, -1),
     (12, 8, -1, 64, 3, 9728, -1),
+    (12, 8, 256, -1, 4, 300, -1),     # automatic storage rule per part
+    (10, 16, 128, 0, 4, 13, 37),
+    (12, 8, -1, -1, 4, 9728, -1),
 ]
 
 
@@ -91,6 +94,7 @@ def test_host_plan_matches_oracle(spg, scale, ef, tw, heavy, rule, mw, mr):
         assert ex["heavy"] == H and ex["WL"] == part["WL"]
         for k in ("rank_row", "rank_chunk", "rank_len", "wl_first", "wl_h", "wl_w", "wl_major"):
             assert np.array_equal(ex[k], part[k]), (p, k)
+        assert ex["rule"] == part["rule"] == (rule if rule != 4 else ex["rule"])
     assert np.array_equal(f.zero_rows(), plan["zero_rows"])
     # the packed slots hold exactly M's entries (values bit-exact)
     r, c, v = f.export_entries()
@@ -293,3 +297,38 @@ def test_tile_coo_option_builds_on_the_host(spg):
     x = np.zeros(n, np.float32)
     with pytest.raises(spg.SpgError):
         b.spmv_tile_coo(x, np.zeros(n, np.float32))
+
+
+def test_automatic_rule_is_the_argmin_of_the_model(spg):
+    # rule 4: each part's storage rule is the first (in the order 1, 0, 2, 3)
+    # whose plan the Algorithm 3 model prices lowest -- checked against the
+    # oracle's model cost of every rule's plan, part by part
+    nlog = 21
+    rng = np.random.default_rng(5)
+    for trial in range(3):
+        perf = rng.uniform(1e9, 5e9, 2 * nlog * nlog)
+        if trial == 1:
+            perf[: nlog * nlog] *= 0.05     # row-major slow: ELL-leaning plans
+        path = _table_file(perf)
+        try:
+            rp, col = graphgen.rmat(11, 8, seed=1 + trial)
+            f = spg.Format(rp, col, kind="pagerank", tile_width=256, max_warps=64, keep_plan=True,
+                           host_only=True, table=path, layout_rule=4)
+        finally:
+            spg.load_table(None)
+            os.unlink(path)
+        n = rp.shape[0] - 1
+        pi, inv = f.perm()
+        M = oracle.build_M(rp, col)
+        rows_p = pi[np.repeat(np.arange(n), np.diff(M[0]))]
+        cols_p = pi[M[1]]
+        ids = np.arange(n, dtype=np.int64)
+        for p in range(f.nparts()):
+            ti = f.tile_info(p)
+            m = (cols_p >= ti["col_begin"]) & (cols_p < ti["col_end"])
+            rl = np.bincount(rows_p[m], minlength=n).astype(np.int64)
+            costs = {r: oracle.plan_cost(ids, rl, -1, 0, 64, r, (nlog, perf), 2e-7, 32)
+                     for r in (1, 0, 2, 3)}
+            best = min(costs.values())
+            want = next(r for r in (1, 0, 2, 3) if costs[r] == best)
+            assert ti["layout_rule"] == want, (trial, p, costs)

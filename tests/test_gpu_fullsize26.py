@@ -67,3 +67,23 @@ def test_pagerank_step_and_solve_scale26(g26):
     p, info = f.pagerank(C, tol=1e-7, max_iter=1000, like=like)
     assert info["last_l1"] < 1e-7 and info["iters"] < 200
     assert abs(p.double().sum().item() - 1.0) <= 1e-5
+
+
+def test_pagerank_fixed_point_certificate_scale26(g26):
+    """||p - p*||_1 <= 1e-6 at the billion-edge size without running the
+    oracle to convergence (about 180 FP64 iterations of several seconds
+    each): one oracle iteration G of Eq. 6 is a contraction with factor c in
+    the L1 norm (column sums of M at most 1 + 2^-24 with FP32 values), so
+    for q = G^k(p),  ||p - p*||_1 <= ||p - q||_1 / (1 - c'^k),  c' = c (1 +
+    2^-23).  The GPU solves to tol 1e-8 (the workload's 1e-7 leaves the
+    iterate up to c/(1-c) * 1e-7 from p*)."""
+    rp, col, M, f = g26
+    p, info = f.pagerank(C, tol=1e-8, max_iter=1000, like=torch.empty(0, device=DEV))
+    assert info["last_l1"] < 1e-8
+    p = p.cpu().numpy().astype(np.float64)
+    k = 6
+    q, _, _ = oracle.pagerank(rp, col, C, tol=0.0, max_iter=k, p_init=p, M=M)
+    c_eff = C * (1.0 + 2.0 ** -23)
+    bound = np.abs(p - q).sum() / (1.0 - c_eff ** k)
+    print(f"scale 26: ||p - p*||_1 <= {bound:.3e} ({info['iters']} iterations)")
+    assert bound <= 1e-6

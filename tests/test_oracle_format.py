@@ -327,3 +327,35 @@ def test_split_chunk_count_hand_computed():
     assert oracle.split_cost_chunks(rl, 128) == 0.0
     assert oracle.split_cost_chunks(rl, 64) == 2.0 + 2.0      # 128 -> 2, 65 -> 2
     assert oracle.split_cost_chunks(rl, 32) == 4.0 + 3.0      # 128 -> 4, 65 -> 3
+
+
+def test_choose_rule_hand_cases():
+    # 64 rows of 4 entries, WL = 128 -> two 4 x 32 workloads.  Constant
+    # table: rules 0, 1, 3 store them column-major (4 x 32 = 128 slots
+    # each), rule 2 row-major (32 x 32 = 1024 each): costs 256, 256, 2048,
+    # 256 -> the first of the cheapest in the order 1, 0, 2, 3 is rule 1
+    ids = np.arange(64, dtype=np.int64)
+    rl = np.full(64, 4, np.int64)
+    costs = [oracle.plan_cost(ids, rl, 0, 128, 1000, r, _const_table(), 0.0) for r in (0, 1, 2, 3)]
+    assert costs == [256.0, 256.0, 2048.0, 256.0]
+    assert oracle.choose_rule(ids, rl, 0, 128, 1000, _const_table(), 0.0) == 1
+    # 32 rows of 32 entries, WL = 1024 -> one 32 x 32 workload: rules 0 and
+    # 2 store it row-major, 1 (tie) and 3 column-major.  Row-major table 2,
+    # column-major 1: 512 for rules 0 and 2, 1024 for 1 and 3 -> rule 0
+    # (before 2 in the order)
+    ids = np.arange(32, dtype=np.int64)
+    rl = np.full(32, 32, np.int64)
+    t = _major_table(2.0, 1.0)
+    assert [oracle.plan_cost(ids, rl, 0, 1024, 1000, r, t, 0.0) for r in (0, 1, 2, 3)] == \
+        [512.0, 1024.0, 512.0, 1024.0]
+    assert oracle.choose_rule(ids, rl, 0, 1024, 1000, t, 0.0) == 0
+    # 10 rows of 64 entries, WL = 64 -> ten 64 x 1 workloads: rules 0, 1, 2
+    # row-major (64 slots each), rule 3 column-major (64 x 32 = 2048 each).
+    # Row-major table 0.001, column-major 1: 640 / 0.001 = 640000 against
+    # 20480 -> rule 3
+    ids = np.arange(10, dtype=np.int64)
+    rl = np.full(10, 64, np.int64)
+    t = _major_table(0.001, 1.0)
+    costs = [oracle.plan_cost(ids, rl, 0, 64, 1000, r, t, 0.0) for r in (0, 1, 2, 3)]
+    assert np.allclose(costs, [640000.0, 640000.0, 640000.0, 20480.0])
+    assert oracle.choose_rule(ids, rl, 0, 64, 1000, t, 0.0) == 3

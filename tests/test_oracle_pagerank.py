@@ -80,3 +80,34 @@ def test_iteration_count_and_warm_start():
     p2, it2, _ = oracle.pagerank(rp, col, C, tol=1e-6, p_init=p)
     assert it2 == 1
     np.testing.assert_allclose(p2, p, atol=1e-7)
+
+
+def test_iteration_is_an_l1_contraction_and_certifies_the_error():
+    # G(p) = c M p + (c * sum_{u dangling} p_u + 1 - c)/n contracts L1
+    # distances by c (M's non-dangling columns sum to 1, dangling mass is
+    # spread): ||G p - G q||_1 <= c ||p - q||_1 for any p, q; hence for any
+    # p, ||p - p*||_1 <= ||p - G^k p||_1 / (1 - c^k) (used to certify the
+    # billion-edge GPU result without converging the oracle there)
+    import graphgen
+    rp, col = graphgen.rmat(11, 8, seed=3)
+    n = rp.shape[0] - 1
+    M = oracle.build_M(rp, col)
+    c = 0.85
+    rng = np.random.default_rng(0)
+    c_eff = c * (1.0 + 2.0 ** -23)
+    for _ in range(5):
+        p = rng.random(n)
+        q = rng.random(n) * rng.integers(0, 2, n)
+        Gp, _, _ = oracle.pagerank(rp, col, c, tol=0.0, max_iter=1, p_init=p, M=M)
+        Gq, _, _ = oracle.pagerank(rp, col, c, tol=0.0, max_iter=1, p_init=q, M=M)
+        assert np.abs(Gp - Gq).sum() <= c_eff * np.abs(p - q).sum() * (1 + 1e-12)
+    p_star, _, _ = oracle.pagerank(rp, col, c, tol=1e-14, M=M)
+    for scale in (1e-3, 1e-6):
+        p = p_star + scale * rng.standard_normal(n) / n
+        for k in (1, 3, 6):
+            qk, _, _ = oracle.pagerank(rp, col, c, tol=0.0, max_iter=k, p_init=p, M=M)
+            cert = np.abs(p - qk).sum() / (1.0 - c_eff ** k)
+            true = np.abs(p - p_star).sum()
+            assert true <= cert * (1 + 1e-9)
+            # and never loose by more than (1 + c^k) / (1 - c^k)
+            assert cert <= (1.0 + c_eff ** k) / (1.0 - c_eff ** k) * true * (1 + 1e-9)
