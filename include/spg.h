@@ -135,10 +135,12 @@ typedef struct {
     /* Path of a performance table (text, see spg_load_table) or NULL for the
      * table built into the library. */
     const char *tune_table_path;
-    /* Kernel option 1: columns of x staged in shared memory per part (the
-     * part's densest ones; the GB300 counterpart of the paper's
-     * texture-cache tile): 0 = auto (49152, i.e. 192 KB), < 0 = off (x
-     * gathered through L1/L2).  The default kernel stages none. */
+    /* Columns of x staged in shared memory per part by kernel option 1 (the
+     * part's densest ones: columns are in decreasing-length order; the GB300
+     * counterpart of the paper's texture-cache tile): 0 = auto (24576, i.e.
+     * 96 KB, which leaves about 156 KB of the SM to the L1 cache that
+     * gathers the other columns), at most 49152; < 0 = off (x gathered
+     * through L1/L2 only). */
     int64_t x_stage_cols;
     /* Distance, in bytes, by which each warp's bulk L2 prefetch of its slots
      * runs ahead of their use (TMA cp.async.bulk.prefetch).  <= 0 = off (the
@@ -156,17 +158,21 @@ typedef struct {
      * Algorithm 3 model sees the capped rectangles.  0 = auto (32),
      * < 0 = no cap (the paper's packing). */
     int64_t max_rows;
-    /* SpMV kernel.  0 (default) and 4: persistent 8-warp blocks -- five per
-     * SM (40 warps) for plain SpMV, four (32 warps, no register spills) for
-     * the fused power-iteration epilogues -- taking claim units from a
-     * counter, x gathered through L1/L2; 1: one persistent 32-warp block per SM with the part's first
-     * x_stage_cols columns of x staged in shared memory (the GB300 form of
-     * the paper's texture-cache tile, Section 3.1 Solution 1); 2: plain
-     * 8-warp blocks, one workload per warp; 3: option 1 with each warp's
-     * slots streamed into a shared-memory ring by TMA bulk copies.
-     * Measured per PageRank iteration on GB300 (options 0 vs 1): R-MAT
-     * scale 22 0.213 vs 0.213 ms, R-MAT scale 26 3.64 vs 4.27 ms, Chung-Lu
-     * 50M 3.55 vs 4.05 ms; banded SpMV 0.24 vs 0.30 ms. */
+    /* SpMV kernel.  0 = auto (the default): option 1, or option 4 when
+     * x_stage_cols < 0.  1: one persistent 32-warp block per SM (parts at
+     * least 1024 columns wide) with the part's first x_stage_cols columns
+     * of x in shared memory, gathered by predicated loads (shared inside the
+     * slice, global past it); warps take claim units from a counter.
+     * 4: persistent 8-warp blocks -- five per SM (40 warps) for plain SpMV,
+     * four (32 warps) for the fused power-iteration epilogues -- with every
+     * gather through L1/L2.  2: plain 8-warp blocks, one workload per warp.
+     * 3: option 1 with each warp's slots streamed into a shared-memory ring
+     * by TMA bulk copies.  Measured per PageRank iteration on GB300
+     * (kernel time, options 1 vs 4): R-MAT scale 22 0.170 vs 0.175 ms,
+     * scale 24 0.757 vs 0.776 ms, scale 26 3.71 vs 3.77 ms; plain SpMV at
+     * scale 22 0.157 vs 0.174 ms.  Scattered 4-byte gathers through L1 cost
+     * one tag lookup per distinct line, which bounds the gather rate; the
+     * slice moves the densest columns' gathers to shared memory. */
     int kernel;
     /* PAGERANK handles only: store column indices alone (4 bytes per slot
      * instead of 8).  M = A^T diag(1/outdeg), so the iteration gathers

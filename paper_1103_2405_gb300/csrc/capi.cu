@@ -332,14 +332,17 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     if (e != cudaSuccess) return cuda_fail(e, "upload");
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     h->stage_cols = o.x_stage_cols < 0 ? 0
-                  : (o.x_stage_cols > 0 ? std::min<int64_t>(o.x_stage_cols, kStagedMaxCols) : kStagedMaxCols);
+                  : (o.x_stage_cols > 0 ? std::min<int64_t>(o.x_stage_cols, kStagedMaxCols) : kStagedDefaultCols);
     h->pf_ahead = o.slab_prefetch > 0 ? (int32_t)std::min<int64_t>(o.slab_prefetch, 1 << 20) : 0;
     h->pf_ahead = (h->pf_ahead + 255) / 256 * 256;
     h->loop_mode = o.loop_mode == 1 ? 1 : 0;
     h->separate_check = o.separate_check != 0;
     h->kernel = (o.kernel >= 0 && o.kernel <= 4) ? o.kernel : 0;
     if (o.x_stage_cols < 0 && h->kernel == 1) h->kernel = 2;   // no shared-memory staging at all
-    if (h->kernel == 0) h->kernel = 4;   // the default: persistent 8-warp blocks
+    // the default: one persistent 32-warp block per SM with the part's
+    // densest x columns in shared memory (option 1); without a slice, the
+    // persistent 8-warp blocks (option 4)
+    if (h->kernel == 0) h->kernel = o.x_stage_cols < 0 ? 4 : 1;
     if (h->kernel == 4) {
         const int b = persist_blocks_per_sm();
         h->persist_blocks = b > 0 ? b : 1;

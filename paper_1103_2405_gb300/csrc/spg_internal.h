@@ -76,6 +76,13 @@ constexpr int kTmaMaxCols = 24576;
 
 // Largest x slice staged in shared memory (floats): 192 KB.
 constexpr int kStagedMaxCols = 49152;
+// Default x slice of the staged kernel (floats): 96 KB, which with the
+// kernel's 2 KB of static shared memory fits the 100 KB shared-memory
+// carve-out and leaves about 156 KB of the SM's 256 KB to the L1 cache --
+// the columns past the slice are gathered through L1, and a 192 KB slice
+// (36 KB of L1 left) measured slower (R-MAT scale 24 PageRank iteration:
+// 0.749 ms with 24K columns, 0.872 ms with 48K, 0.776 ms with none).
+constexpr int kStagedDefaultCols = 24576;
 
 // Split-row scratch shared by all parts of a format.
 struct SplitView {
