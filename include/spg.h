@@ -102,11 +102,13 @@ typedef struct {
      * after another),
      * 2 = every workload row-major (the CSR-vector special case), 3 = every
      * workload column-major (the ELL special case; Section 5),
-     * 4 = automatic (the default when opts is NULL): per part, the rule of
-     * 0-3 whose plan -- its own split threshold and Algorithm 2 workload
-     * size -- the Algorithm 3 model prices lowest (first of 1, 0, 2, 3 on a
-     * tie); spg_tile_info reports the rule each part got.  A zeroed
-     * options struct selects rule 0: set 4 for the automatic choice. */
+     * 4 = automatic: per part, the rule of 0-3 whose plan -- its own split
+     * threshold and Algorithm 2 workload size -- the Algorithm 3 model
+     * prices lowest (first of 1, 0, 2, 3 on a tie); spg_tile_info reports
+     * the rule each part got.  Rule 1 is the default (opts NULL): the model
+     * ranks the rules as measured at R-MAT scale 22, but at scale 26 it
+     * picks rule 0 for the largest part, measured 3 % slower there.  A
+     * zeroed options struct selects rule 0. */
     int layout_rule;
     /* Maximum resident warps of the whole GPU used by Algorithms 2-3.
      * 0 = query the current device (SMs x resident warps of the kernel). */

@@ -202,7 +202,7 @@ class Format:
     logits (kind 'weighted').  Build options map 1:1 to spg_build_opts."""
 
     def __init__(self, rowptr, col, val=None, kind="pagerank", tile_width=0, wl=0, heavy_row=-1,
-                 layout_rule=4, max_warps=0, vec_width=1, build_transpose=False, keep_plan=False,
+                 layout_rule=1, max_warps=0, vec_width=1, build_transpose=False, keep_plan=False,
                  keep_csr=False, host_only=False, split_cost=0.0, table=None, x_stage_cols=0,
                  slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, pattern_only=False,
                  row_part=None, part_id=0, nparts=None, unit_slots=0, separate_check=False,
@@ -465,7 +465,7 @@ class BatchFormat:
     """Many independent graphs in one handle (spg_build_batch): one
     tiled-composite sweep per iteration over all of them."""
 
-    def __init__(self, graphs, heavy_row=-1, layout_rule=4, max_warps=0, x_stage_cols=0,
+    def __init__(self, graphs, heavy_row=-1, layout_rule=1, max_warps=0, x_stage_cols=0,
                  slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, host_only=False, table=None,
                  claim_order=0, stream=None):
         L = lib()

@@ -370,7 +370,7 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
         spg_build_opts o;
         std::memset(&o, 0, sizeof o);
         o.heavy_row = -1;
-        o.layout_rule = kAutoRule;
+        o.layout_rule = 1;
         if (opts_in) o = *opts_in;
         if (kind < SPG_KIND_MATRIX || kind > SPG_KIND_WEIGHTED) return fail(SPG_ERR_INVALID, "bad kind");
         std::vector<int64_t> hrp;
@@ -403,7 +403,7 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
         prm.tile_width = resolve_tile_width(o, l2);
         prm.wl = o.wl;
         prm.heavy = o.heavy_row;
-        prm.layout_rule = (o.layout_rule >= 0 && o.layout_rule <= kAutoRule) ? o.layout_rule : kAutoRule;
+        prm.layout_rule = (o.layout_rule >= 0 && o.layout_rule <= kAutoRule) ? o.layout_rule : 1;
         prm.max_warps = o.max_warps > 0 ? o.max_warps : (h->host_only ? 9728 : query_max_warps());
         prm.max_rows = o.max_rows < 0 ? 0 : (o.max_rows > 0 ? o.max_rows : kDefaultMaxRows);
         if (o.split_cost > 0) prm.split_cost = o.split_cost;
@@ -1645,7 +1645,7 @@ extern "C" spg_status spg_build_batch(const spg_csr *graphs, int count,
         spg_build_opts o;
         std::memset(&o, 0, sizeof o);
         o.heavy_row = -1;
-        o.layout_rule = kAutoRule;
+        o.layout_rule = 1;
         if (opts_in) o = *opts_in;
         cudaStream_t s = (cudaStream_t)stream;
         std::unique_ptr<spg_format_t> h(new spg_format_t());
@@ -1698,7 +1698,7 @@ extern "C" spg_status spg_build_batch(const spg_csr *graphs, int count,
         prm.tile_width = 0;
         prm.wl = o.wl;
         prm.heavy = o.heavy_row;
-        prm.layout_rule = (o.layout_rule >= 0 && o.layout_rule <= kAutoRule) ? o.layout_rule : kAutoRule;
+        prm.layout_rule = (o.layout_rule >= 0 && o.layout_rule <= kAutoRule) ? o.layout_rule : 1;
         prm.max_warps = o.max_warps > 0 ? o.max_warps : (h->host_only ? 9728 : query_max_warps());
         prm.max_rows = o.max_rows < 0 ? 0 : (o.max_rows > 0 ? o.max_rows : kDefaultMaxRows);
         prm.unit_slots = o.unit_slots > 0 ? o.unit_slots : kDefaultUnitSlots;
