@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--impl", default="spg", choices=["spg", "reference"])
     ap.add_argument("--workload", default="rmat26", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--partition", default="replicas", choices=["replicas", "rows"],
+                    help="replicas: every rank solves the whole workload (default); rows: the "
+                         "ranks share one PageRank by the Section 3.2 row partition, exchanging "
+                         "row slices every iteration (torch.distributed)")
     ap.add_argument("--host-loop", action="store_true",
                     help="iterate with direct launches (host loop) instead of the CUDA-graph "
                          "WHILE loop, so a kernel profiler can attribute every launch")
@@ -524,10 +528,70 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_rows(args):
+    """One PageRank shared by the ranks (Section 3.2): rank r holds the rows
+    the bitonic partition deals it, every iteration exchanges the ranks'
+    row slices (all-gather) and partial sums (rank-order all-reduce); the
+    whole job's throughput is 2 nnz per iteration over the slowest rank's
+    time.  One process per GPU under torchrun (NCCL), or one rank alone."""
+    import torch
+    import paper_1103_2405_gb300 as spg
+    from paper_1103_2405_gb300 import rows
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    rp, col = graph(args.workload)
+    n, nnz = int(rp.shape[0] - 1), int(rp[-1])
+    t0 = time.perf_counter()
+    fmt, row_part, positions, inv = rows.build_rank(rp, col, rank, world)
+    build_s = time.perf_counter() - t0
+    me = rows.DeviceRank(fmt, rank, positions, dev)
+    ex = rows.DistExchange([len(p) for p in positions]) if world > 1 else rows.LocalExchange()
+    rows.pagerank_rows([me], ex, damping=DAMPING, tol=0.0, max_iter=max(3, args.warmup))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    L0 = spg.launch_count()
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        rows.pagerank_rows([me], ex, damping=DAMPING, tol=0.0, max_iter=args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = spg.launch_count() - L0
+    t_ms, _ = aggregate_ranks(ev0.elapsed_time(ev1), 0.0, world, dev)
+    ms = t_ms / args.steps
+    alg = 8 * nnz + 16 * n
+    peak = float(peaks().get("hbm_gbs", 6800.0))
+    if rank == 0:
+        line = {"metric": "SpMV GFLOP/s (2*nnz) in PageRank iterations", "value": 2.0 * nnz / (ms * 1e-3) / 1e9,
+                "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.workload]["desc"] + ", row-partitioned",
+                           "n": n, "nnz": nnz, "ranks": world, "rows_per_rank": [len(p) for p in positions],
+                           "build_s": build_s, "l2": "inputs larger than L2"},
+                "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9 / world, "peak": peak,
+                             "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / world / peak, "traffic": None,
+                             "kernel": "rank step (k_part_staged<EPI_PAGERANK> + check) + slice exchange, "
+                                       "per GPU"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.partition == "rows":
+        return run_rows(args)
     if args.workload in ("rwr64", "batch512", "adjoint20", "hits22", "rwr22"):
         return run_secondary(args)
     if args.workload in UNSTRUCTURED:

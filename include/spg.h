@@ -367,6 +367,32 @@ spg_status spg_pagerank_ranks(const spg_handle *ranks, int P, float damping, dou
                               int max_iter, const float *p0, float *p_out, spg_iter_info *info,
                               void *stream);
 
+/* One PageRank iteration (Eq. 6) of ONE rank of the Section 3.2 row
+ * partition, for a driver that runs every rank in its own process (or on its
+ * own device) and exchanges row slices between iterations itself.  h: a
+ * device PAGERANK handle built with row_part / part_id = this rank (or with
+ * no row_part: every row); x_perm: the whole current iterate (n floats,
+ * the handle's permuted order, device); y_perm: device output of n floats,
+ * of which only this rank's rows are written.  delta: the dangling mass of
+ * x over ALL rows (the sum over ranks of the previous step's partial[1];
+ * for the uniform start, the sum over dangling nodes of 1/n).  Writes, in
+ * partial (host double[2]): this rank's L1 change sum |y'_v - x'_v| and its
+ * rows' dangling mass sum of y'_v over dangling v, each summed in a fixed
+ * order.  Synchronises `stream`.  Errors: SPG_ERR_INVALID for a non-device
+ * or aliased vector, bad damping or negative delta; SPG_ERR_UNSUPPORTED for
+ * a pattern_only handle. */
+spg_status spg_pagerank_rank_step(spg_handle h, float damping, double delta, const float *x_perm,
+                                  float *y_perm, double *partial, void *stream);
+
+/* Row slices of the Section 3.2 all-gather (device pointers, idx int32 of
+ * count positions in [0, n)): pack slice[i] = full[idx[i]]; unpack
+ * full[idx[i]] = slice[i].  Asynchronous on `stream`; count 0 is a no-op;
+ * SPG_ERR_INVALID for a negative count or a host pointer. */
+spg_status spg_pack_slice(int64_t count, const int32_t *idx, const float *full, float *slice,
+                          void *stream);
+spg_status spg_unpack_slice(int64_t count, const int32_t *idx, const float *slice, float *full,
+                            void *stream);
+
 /* Random Walk with Restart, Appendix F Eq. 9 on M (personalised PageRank):
  * r <- c M r + [v == s] (c * dangling mass + 1 - c), r(0) = e_s, for each of
  * the k restart nodes seeds[0..k) (host int32, original ids).  k == 1 runs

@@ -79,7 +79,8 @@ EXPORTS = ["spg_build_format", "spg_destroy", "spg_format_info", "spg_tile_info"
            "spg_batch_offsets", "spg_batch_pagerank",
            "spg_baseline_spmv", "spg_baseline_pagerank", "spg_time_parts", "spg_load_table", "spg_launch_count",
            "spg_status_string", "spg_last_error", "spg_version", "spg_spmv_permuted_noalloc",
-           "spg_partition_rows", "spg_pagerank_ranks", "spg_spmv_tile_coo"]
+           "spg_partition_rows", "spg_pagerank_ranks", "spg_spmv_tile_coo", "spg_pagerank_rank_step",
+           "spg_pack_slice", "spg_unpack_slice"]
 
 _lib = None
 
@@ -122,6 +123,9 @@ def lib():
             "spg_load_table": [ctypes.c_char_p],
             "spg_partition_rows": [i64, P, i32, P],
             "spg_pagerank_ranks": [P, i32, f32, f64, i32, P, P, ctypes.POINTER(IterInfo), P],
+            "spg_pagerank_rank_step": [P, f32, f64, P, P, P, P],
+            "spg_pack_slice": [i64, P, P, P, P],
+            "spg_unpack_slice": [i64, P, P, P, P],
         }
         for name, args in sig.items():
             getattr(L, name).argtypes = args
@@ -391,6 +395,14 @@ class Format:
                                        float(beta), _stream(stream)))
         return y
 
+    def rank_step(self, damping, delta, xp, yp, stream=None):
+        """One Eq. 6 iteration of this rank's rows (spg_pagerank_rank_step):
+        returns (L1 change over the rank's rows, dangling mass of its rows)."""
+        part = (ctypes.c_double * 2)()
+        _check(lib().spg_pagerank_rank_step(self._h, float(damping), float(delta), _ptr(xp)[0],
+                                            _ptr(yp)[0], part, _stream(stream)))
+        return float(part[0]), float(part[1])
+
     def time_parts(self, mode=0, reps=20, stream=None):
         """Mean launch duration (ms) of each part's kernel (CUDA events)."""
         ms = np.zeros(self.nparts(), np.float32)
@@ -444,6 +456,20 @@ def partition_rows(row_len, P):
     part = np.empty(rl.shape[0], np.int32)
     _check(lib().spg_partition_rows(rl.shape[0], _ptr(rl)[0], int(P), _ptr(part)[0]))
     return part
+
+
+def pack_slice(idx, full, slice_, stream=None):
+    """slice[i] = full[idx[i]] on the device (spg_pack_slice)."""
+    _check(lib().spg_pack_slice(int(idx.shape[0]), _ptr(idx)[0], _ptr(full)[0], _ptr(slice_)[0],
+                                _stream(stream)))
+    return slice_
+
+
+def unpack_slice(idx, slice_, full, stream=None):
+    """full[idx[i]] = slice[i] on the device (spg_unpack_slice)."""
+    _check(lib().spg_unpack_slice(int(idx.shape[0]), _ptr(idx)[0], _ptr(slice_)[0], _ptr(full)[0],
+                                  _stream(stream)))
+    return full
 
 
 def pagerank_ranks(ranks, damping=0.85, tol=1e-8, max_iter=1000, p0=None, out=None, like=None,

@@ -1384,6 +1384,64 @@ extern "C" spg_status spg_pagerank_ranks(const spg_handle *ranks, int P, float d
     return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
 }
 
+// ----------------------------------------- one rank's step, row slices --
+
+extern "C" spg_status spg_pagerank_rank_step(spg_handle h, float damping, double delta,
+                                             const float *x_perm, float *y_perm, double *partial,
+                                             void *stream)
+{
+    if (!h || h->host_only || h->kind != SPG_KIND_PAGERANK)
+        return fail(SPG_ERR_INVALID, "rank step needs a device PAGERANK handle");
+    if (h->fwd.pattern) return fail(SPG_ERR_UNSUPPORTED, "rank step needs stored values (no pattern_only)");
+    if (!x_perm || !y_perm || x_perm == y_perm || !partial || !is_device_ptr(x_perm) || !is_device_ptr(y_perm))
+        return fail(SPG_ERR_INVALID, "x' and y' must be distinct device vectors; partial a host array");
+    if (!(damping >= 0.f && damping < 1.f) || !(delta >= 0.0))
+        return fail(SPG_ERR_INVALID, "bad damping or dangling mass");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->fwd.n;
+    spg_status st = ensure_vectors(h, N);
+    if (st != SPG_OK) return st;
+    // the rank's kernels on a state whose current iterate is the caller's x'
+    // and whose next one is the caller's y'; the separate check kernel then
+    // sums this rank's block partials in a fixed order
+    IterState hs = make_state(h, damping, 0.0, 1, N, const_cast<float *>(x_perm), y_perm);
+    hs.delta = delta;
+    CK(cudaMemcpyAsync(h->d_state, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
+    const spg_format_t::Views &V = get_views(h, true);
+    const int nred = nred_of(h, V);
+    launch_parts(h, EPI_PAGERANK, nullptr, nullptr, h->d_state, h->red.p, s);
+    launch_check(EPI_PAGERANK, h->d_state, h->red.p, nred, 0, 0, s);
+    CK(cudaMemcpyAsync(h->hs_pinned, h->d_state, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    partial[0] = h->hs_pinned->l1;
+    partial[1] = h->hs_pinned->delta;
+    return take_status(h);
+}
+
+extern "C" spg_status spg_pack_slice(int64_t count, const int32_t *idx, const float *full, float *slice,
+                                     void *stream)
+{
+    if (count < 0) return fail(SPG_ERR_INVALID, "negative count");
+    if (count == 0) return SPG_OK;
+    if (!idx || !full || !slice || !is_device_ptr(idx) || !is_device_ptr(full) || !is_device_ptr(slice))
+        return fail(SPG_ERR_INVALID, "pack_slice takes device pointers");
+    launch_gather(count, idx, full, slice, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return SPG_OK;
+}
+
+extern "C" spg_status spg_unpack_slice(int64_t count, const int32_t *idx, const float *slice, float *full,
+                                       void *stream)
+{
+    if (count < 0) return fail(SPG_ERR_INVALID, "negative count");
+    if (count == 0) return SPG_OK;
+    if (!idx || !full || !slice || !is_device_ptr(idx) || !is_device_ptr(full) || !is_device_ptr(slice))
+        return fail(SPG_ERR_INVALID, "unpack_slice takes device pointers");
+    launch_scatter_axpby(count, idx, slice, full, 1.f, 0.f, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return SPG_OK;
+}
+
 // ------------------------------------------------------------ baselines --
 
 extern "C" spg_status spg_baseline_spmv(spg_handle h, spg_baseline which, const float *x, float *y,
