@@ -256,6 +256,9 @@ typedef struct {
     int64_t nnz;                /* non-zeros in the part */
     double predicted_ms;
     int64_t layout_rule;        /* storage rule the part was built with (0-3) */
+    double slice_share;         /* share of the part's entries in its first x_stage_cols
+                                   columns; kernel option 1 stages the x slice for the
+                                   part only when it is at least 0.10 */
 } spg_tile_info_t;
 
 /* ---------------------------------------------------------------- build -- */

@@ -68,7 +68,8 @@ class _Info(ctypes.Structure):
 class _TileInfo(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in
                 ("col_begin", "col_end", "heavy", "wl", "nvirt", "nwl", "nnz")] + \
-               [("predicted_ms", ctypes.c_double), ("layout_rule", ctypes.c_int64)]
+               [("predicted_ms", ctypes.c_double), ("layout_rule", ctypes.c_int64),
+                ("slice_share", ctypes.c_double)]
 
 
 # Every symbol include/spg.h declares.

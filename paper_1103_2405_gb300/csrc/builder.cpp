@@ -544,6 +544,15 @@ bool build_layout(const ColumnSource &src, const BuildParams &prm, Layout &L, st
             pn += l;
         }
         ph.nnz = pn;
+        {
+            int64_t all = 0, head = 0;
+            for (int64_t c = ph.c0; c < ph.c1; ++c) {
+                const int64_t l = collen[(size_t)L.inv[(size_t)c]];
+                all += l;
+                if (c < ph.c0 + prm.stage_cols) head += l;
+            }
+            ph.slice_share = all > 0 ? (double)head / (double)all : 0.0;
+        }
         // storage rule of the part: the given one, or (kAutoRule) the rule
         // of rules 0-3 whose plan -- its own split threshold and workload
         // size -- the Algorithm 3 model prices lowest (Section 5: CSR-vector

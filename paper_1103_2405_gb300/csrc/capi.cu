@@ -324,6 +324,14 @@ static int64_t query_max_warps()
 
 // ----------------------------------------------------------------- build --
 
+// Columns of the shared-memory x slice (option 1): x_stage_cols, 0 = the
+// default, < 0 = none.
+static int64_t resolve_stage_cols(const spg_build_opts &o)
+{
+    return o.x_stage_cols < 0 ? 0
+         : (o.x_stage_cols > 0 ? std::min<int64_t>(o.x_stage_cols, kStagedMaxCols) : kStagedDefaultCols);
+}
+
 // Upload the forward layout and set up the launch-time state of a handle.
 static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream_t s)
 {
@@ -331,8 +339,7 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     if (e == cudaErrorMemoryAllocation) return fail(SPG_ERR_OOM, "device memory for the format");
     if (e != cudaSuccess) return cuda_fail(e, "upload");
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-    h->stage_cols = o.x_stage_cols < 0 ? 0
-                  : (o.x_stage_cols > 0 ? std::min<int64_t>(o.x_stage_cols, kStagedMaxCols) : kStagedDefaultCols);
+    h->stage_cols = resolve_stage_cols(o);
     h->pf_ahead = o.slab_prefetch > 0 ? (int32_t)std::min<int64_t>(o.slab_prefetch, 1 << 20) : 0;
     h->pf_ahead = (h->pf_ahead + 255) / 256 * 256;
     h->loop_mode = o.loop_mode == 1 ? 1 : 0;
@@ -343,7 +350,8 @@ static spg_status device_setup(spg_handle h, const spg_build_opts &o, cudaStream
     // densest x columns in shared memory (option 1); without a slice, the
     // persistent 8-warp blocks (option 4)
     if (h->kernel == 0) h->kernel = o.x_stage_cols < 0 ? 4 : 1;
-    if (h->kernel == 4) {
+    {   // option 4's blocks per SM (also option 1's choice for parts whose
+        // slice would serve few entries)
         const int b = persist_blocks_per_sm();
         h->persist_blocks = b > 0 ? b : 1;
     }
@@ -409,6 +417,7 @@ extern "C" spg_status spg_build_format(const spg_csr *csr, spg_kind kind,
         if (o.split_cost > 0) prm.split_cost = o.split_cost;
         prm.keep_plan = o.keep_plan != 0;
         prm.track_edges = kind == SPG_KIND_WEIGHTED;
+        prm.stage_cols = resolve_stage_cols(o);
         if (o.pattern_only && kind != SPG_KIND_PAGERANK)
             return fail(SPG_ERR_INVALID, "pattern_only needs a PAGERANK handle");
         prm.pattern_only = o.pattern_only != 0;
@@ -610,6 +619,7 @@ extern "C" spg_status spg_tile_info(spg_handle h, int64_t part, spg_tile_info_t 
     info->nnz = p.nnz;
     info->predicted_ms = p.predicted_s * 1e3;
     info->layout_rule = p.rule;
+    info->slice_share = p.slice_share;
     return SPG_OK;
 }
 
@@ -739,7 +749,11 @@ static PartView part_view(spg_handle h, const Layout &L, size_t p, bool staged, 
     pv.pf_ahead = h->pf_ahead;
     pv.status = h->d_status;
     const int64_t width = ph.c1 - ph.c0;
-    if (staged && h->kernel == 4 && ph.nwl_total > 0) {
+    // option 1 stages the slice only where it serves a useful share of the
+    // part's gathers; elsewhere (a sparse remainder of low-degree columns,
+    // a banded or stencil matrix) the slice-free persistent kernel runs
+    const bool slice_pays = ph.slice_share >= kSliceMinShare;
+    if (staged && (h->kernel == 4 || (h->kernel == 1 && !slice_pays)) && ph.nwl_total > 0) {
         // persistent 8-warp blocks, several per SM, no x slice
         pv.persist = 1;
         pv.xs_cols = 0;
@@ -1764,6 +1778,7 @@ extern "C" spg_status spg_build_batch(const spg_csr *graphs, int count,
         prm.claim_order = o.claim_order;
         if (o.split_cost > 0) prm.split_cost = o.split_cost;
         prm.keep_plan = o.keep_plan != 0;
+        prm.stage_cols = resolve_stage_cols(o);
         prm.seg_off = h->goff.data();
         prm.nseg = count;
         std::string err;

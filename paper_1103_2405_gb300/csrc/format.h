@@ -45,6 +45,9 @@ struct BuildParams {
     // [seg_off[g], seg_off[g+1]); the degree order is taken within each segment
     const int64_t *seg_off = nullptr;
     int64_t nseg = 0;
+    // columns of the shared-memory x slice the kernel would stage per part
+    // (for PartHost::slice_share; 0 = none)
+    int64_t stage_cols = 0;
     // claim units of the persistent kernels: consecutive workloads grouped
     // until their cost (padded slots + 4 per row) reaches this; <= 1 = one
     // workload per unit
@@ -69,6 +72,9 @@ struct PartHost {
     int64_t c0 = 0, c1 = 0;
     int64_t heavy = 0, wl = 0, nnz = 0, nvirt = 0;
     int32_t rule = 1;         // storage rule the part was built with (0-3)
+    // share of the part's entries (all rows) in its first stage_cols columns:
+    // what a shared-memory x slice of that many columns would serve
+    double slice_share = 0.0;
     int64_t nwl = 0;          // regular workloads
     int64_t nwl_total = 0;    // + zero-row workloads
     int64_t unit_off = 0, nunits = 0;   // claim units: units[unit_off .. unit_off + nunits] (+ end)

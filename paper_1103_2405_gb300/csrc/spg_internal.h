@@ -83,6 +83,12 @@ constexpr int kStagedMaxCols = 49152;
 // (36 KB of L1 left) measured slower (R-MAT scale 24 PageRank iteration:
 // 0.749 ms with 24K columns, 0.872 ms with 48K, 0.776 ms with none).
 constexpr int kStagedDefaultCols = 24576;
+// Option 1 runs the slice kernel on a part only when the slice's columns
+// hold at least this share of the part's entries (R-MAT 22-26: 37-23 % in
+// the first part; R-MAT 26's second part 0.3 %, measured 0.119 ms with the
+// slice against 0.110 ms without; banded and stencil matrices well under
+// 1 %); the other parts run the slice-free persistent kernel (option 4).
+constexpr double kSliceMinShare = 0.10;
 
 // Split-row scratch shared by all parts of a format.
 struct SplitView {

@@ -332,3 +332,26 @@ def test_automatic_rule_is_the_argmin_of_the_model(spg):
             best = min(costs.values())
             want = next(r for r in (1, 0, 2, 3) if costs[r] == best)
             assert ti["layout_rule"] == want, (trial, p, costs)
+
+
+def test_slice_share_is_the_densest_columns_share_of_entries(spg):
+    # the first x_stage_cols columns of a part (decreasing column length)
+    # hold this share of its entries; option 1 stages the slice only where
+    # it is >= 0.10 -- recomputed here from the out-degrees (the column
+    # lengths of M)
+    rp, col = graphgen.rmat(14, 8, seed=1)
+    deg = np.sort(np.diff(rp))[::-1].astype(np.int64)
+    for S, tw in ((1024, -1), (4096, -1), (512, 2048)):
+        f = spg.Format(rp, col, kind="pagerank", host_only=True, x_stage_cols=S, tile_width=tw)
+        for p in range(f.nparts()):
+            ti = f.tile_info(p)
+            seg = deg[ti["col_begin"]:ti["col_end"]]
+            want = seg[:S].sum() / seg.sum() if seg.sum() > 0 else 0.0
+            assert abs(ti["slice_share"] - want) <= 1e-12, (S, p)
+    # a directed star: every entry of M lies in the centre's column
+    n = 1000
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = n - 1
+    col = np.arange(1, n, dtype=np.int32)
+    f = spg.Format(rp, col, kind="pagerank", host_only=True, x_stage_cols=1, tile_width=-1)
+    assert f.tile_info(0)["slice_share"] == 1.0
