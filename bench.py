@@ -363,7 +363,7 @@ def run_secondary(args):
                "forward_plus_gradient_ms_tol_1e-8": full}
         extra = {"roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
                               "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak,
-                              "traffic": None, "kernel": "k_part<EPI_ADJ> + check per iteration"},
+                              "traffic": None, "kernel": "k_part_staged<EPI_ADJ> (transposed layout, fused check)"},
                  "e2e": None}
     extra["gpu_launches"] = spg.launch_count() - L0
     extra["clocks"] = clk.summary()
