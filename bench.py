@@ -173,23 +173,33 @@ def batch_graphs(count=512):
             for g, n in enumerate(sizes)]
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
-# capture summarised under profiles/, keyed by workload, with the hash of
-# the kernel source's code (kernel_source_sha) the counters were taken on:
-# reported only while that code is unchanged (null otherwise).
+# DRAM bytes (read + write) of the dominant kernel per iteration (all its
+# part launches), from the ncu captures summarised under profiles/, keyed by
+# workload, with the hash of the kernel code (kernel_source_sha) the
+# counters were taken on: reported only while that code is unchanged (null
+# otherwise).
 NCU_TRAFFIC = {
-    "rmat22": (572_968_960, "d5bc1293034c72376cf49e2ec72f8cca1184170f566120643e1c1d2d8faafd25"),
+    "rmat26": (12_302_540_000, "ba472c0b038e0aaaca29cbe5540cc030fb94f62aca2260d0039d32339c4c6ca2"),
+    "rmat24": (2_569_484_000, "ba472c0b038e0aaaca29cbe5540cc030fb94f62aca2260d0039d32339c4c6ca2"),
 }
 
 
 def kernel_source_sha():
-    """SHA-256 of the kernel source's code: line comments and blank lines
-    removed, so that an edit of comments alone keeps the counters valid."""
+    """SHA-256 of the code of the SpMV / power-iteration kernels: kernels.cu
+    with line comments and blank lines removed, and without its SpMM
+    section (the k-vector kernels, which the PageRank iteration does not
+    run), so that an edit of comments or of the SpMM alone keeps the
+    counters valid."""
     import hashlib
     import re
     path = os.path.join(ROOT, "paper_1103_2405_gb300", "csrc", "kernels.cu")
     with open(path, encoding="utf-8") as fh:
-        lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in fh]
+        text = fh.read()
+    a = text.find("// " + "-" * 66 + " SpMM --")
+    b = text.find("// " + "-" * 65 + " check --")
+    if 0 <= a < b:
+        text = text[:a] + text[b:]
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
     code = "\n".join(ln for ln in lines if ln)
     return hashlib.sha256(code.encode()).hexdigest()
 
