@@ -644,6 +644,10 @@ def main():
     # ---- dominant kernel: the fused PageRank tiled-composite kernel, alone
     part_ms = f.time_parts(mode=1, reps=max(20, args.steps // 2))
     raw_ms = f.time_parts(mode=0, reps=max(20, args.steps // 2))
+    # the median of single iterations (one event pair around each part's
+    # launch, parts summed), beside the mean of the back-to-back launches
+    singles = [float(f.time_parts(mode=1, reps=1).sum()) for _ in range(31)]
+    k_ms_median = float(np.median(singles))
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -660,6 +664,7 @@ def main():
                 "traffic": ncu_traffic(args.workload),
                 "kernel": "k_part_staged<EPI_PAGERANK> (fused PageRank SpMV, one launch per part)",
                 "kernel_ms": k_ms,
+                "kernel_ms_median_of_31": k_ms_median,
                 "alg_bytes_per_launch": alg_bytes,
                 # the gather upper bound: every entry's x read from DRAM
                 # (4 bytes per entry instead of x once)
