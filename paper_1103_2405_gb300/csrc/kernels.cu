@@ -1332,6 +1332,223 @@ __device__ __forceinline__ void spmm_block(const Workload &d, const uint2 *__res
     }
 }
 
+// ---- k a multiple of 64: a half-warp per stored entry, 16 bytes per lane
+// (the form every k % 64 == 0 call takes; the float2 form above serves the
+// other k).  The SpMM is bound by instruction issue, not by the gather's
+// memory latency (ncu: 1.62G warp instructions per RWR iteration at R-MAT
+// scale 22 in the float2 form, issue 43 % busy, 4.2 long-scoreboard cycles
+// per issue); this form measured 2.62 ms per RWR k = 64 iteration against
+// 3.03 ms.
+// Lane l serves half h = l / 16 and column quad q = l % 16 (columns
+// c0 + 4q .. c0 + 4q + 3 of the 64-column chunk), so one warp instruction
+// gathers the 256-byte X rows of two entries -- half the shuffles, address
+// arithmetic and loads per entry of the float2 form, and no column bounds
+// checks.  Sums go back to the float2-per-lane layout (columns c0 + 2l,
+// c0 + 2l + 1) for the same row epilogue.
+
+#ifndef SPG_SPMM4_ROWU
+#define SPG_SPMM4_ROWU 8
+#endif
+#ifndef SPG_SPMM4_BLKU
+#define SPG_SPMM4_BLKU 4
+#endif
+constexpr int kSpmm4RowU = SPG_SPMM4_ROWU;   // entry pairs gathered together, row-major path
+constexpr int kSpmm4BlkU = SPG_SPMM4_BLKU;   // row pairs gathered together per step, block path
+
+__device__ __forceinline__ float4 gather4q(const float *__restrict__ Xq, int c, int k)
+{
+    if (c < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return __ldg(reinterpret_cast<const float4 *>(Xq + (int64_t)c * k));
+}
+
+__device__ __forceinline__ void fma4(float4 &a, float v, const float4 &p)
+{
+    a.x = fmaf(v, p.x, a.x);
+    a.y = fmaf(v, p.y, a.y);
+    a.z = fmaf(v, p.z, a.z);
+    a.w = fmaf(v, p.w, a.w);
+}
+
+// Row-major workload: entries 2t and 2t + 1 of each 32-entry batch go to the
+// two halves; the halves' sums are added at the end of the row.
+template <int MODE>
+__device__ __forceinline__ void spmm_rows4(const Workload &d, const uint2 *__restrict__ slab,
+                                           const uint32_t *__restrict__ rows, const EpiK &E,
+                                           const SplitView &sv, const float *__restrict__ X,
+                                           float *__restrict__ Y, int k, int lane,
+                                           const int32_t *seeds, const double *delta_k,
+                                           double *redk, FSum *acc4)
+{
+    const uint2 pad = make_uint2(0xffffffffu, 0u);
+    const int h = lane >> 4, q = lane & 15;
+    for (int c0 = 0; c0 < k; c0 += 64) {
+        const float *Xq = X + c0 + 4 * q;
+        const int j0 = c0 + 2 * lane;
+        for (int i = 0; i < d.h; ++i) {
+            const uint32_t rid = __ldg(rows + i);
+            const RowPreK pre = prefetch_row_k<MODE>(rid, true, X, Y, k, j0);
+            const uint2 *rs = slab + (int64_t)i * d.w;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint2 nxt = d.w > 0 ? __ldcs(rs + lane) : pad;
+            for (int e0 = 0; e0 < d.w; e0 += 32) {
+                const uint2 ent = nxt;
+                const int cnt = __popc(__ballot_sync(kFull, (int)ent.x >= 0));
+                nxt = (cnt == 32 && e0 + 32 < d.w) ? __ldcs(rs + e0 + 32 + lane) : pad;
+#pragma unroll
+                for (int t0 = 0; t0 < 16; t0 += kSpmm4RowU) {
+                    float4 p[kSpmm4RowU];
+#pragma unroll
+                    for (int u = 0; u < kSpmm4RowU; ++u) {
+                        const int e = 2 * (t0 + u) + h;
+                        const int c = __shfl_sync(kFull, (int)ent.x, e);
+                        p[u] = gather4q(Xq, e < cnt ? c : -1, k);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kSpmm4RowU; ++u) {
+                        const int e = 2 * (t0 + u) + h;
+                        const float v = __shfl_sync(kFull, __uint_as_float(ent.y), e);
+                        fma4(a, e < cnt ? v : 0.f, p[u]);
+                    }
+                }
+                if (cnt < 32) break;
+            }
+            a.x += __shfl_xor_sync(kFull, a.x, 16);
+            a.y += __shfl_xor_sync(kFull, a.y, 16);
+            a.z += __shfl_xor_sync(kFull, a.z, 16);
+            a.w += __shfl_xor_sync(kFull, a.w, 16);
+            // lane l takes columns 2l, 2l + 1: half of quad l / 2
+            const float bx = __shfl_sync(kFull, a.x, lane >> 1), by = __shfl_sync(kFull, a.y, lane >> 1);
+            const float bz = __shfl_sync(kFull, a.z, lane >> 1), bw = __shfl_sync(kFull, a.w, lane >> 1);
+            const float a0 = (lane & 1) ? bz : bx, a1 = (lane & 1) ? bw : by;
+            spmm_finish_pre<MODE>(E, sv, rid, a0, a1, pre, c0, k, lane, X, Y, seeds, delta_k, redk, acc4);
+        }
+    }
+}
+
+// Column-major block of 32 rows: half h sums rows 2t + h (t = 0..15) for its
+// column quad, step by step (the same order of the row's entries as the
+// float2 form), then writes the sums to the warp's tile in the float2-per-
+// lane layout for the epilogue.
+template <int MODE>
+__device__ __forceinline__ void spmm_block4(const Workload &d, const uint2 *__restrict__ slab,
+                                            const uint32_t *__restrict__ rows, const EpiK &E,
+                                            const SplitView &sv, const float *__restrict__ X,
+                                            float *__restrict__ Y, int k, int lane,
+                                            const int32_t *seeds, const double *delta_k,
+                                            double *redk, FSum *acc4, float2 *tile)
+{
+    const uint2 pad = make_uint2(0xffffffffu, 0u);
+    const int hp = (d.h + 31) & ~31;
+    const int h = lane >> 4, q = lane & 15;
+    for (int b = 0; b < hp; b += 32) {
+        const uint32_t my_rid = b + lane < d.h ? __ldg(rows + b + lane) : 0u;
+        const uint2 *blk = slab + (int64_t)b * d.w;
+        const int nr = min(32, d.h - b);
+        for (int c0 = 0; c0 < k; c0 += 64) {
+            const float *Xq = X + c0 + 4 * q;
+            const int j0 = c0 + 2 * lane;
+            float4 acc[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint2 nxt = d.w > 0 ? __ldcs(blk + lane) : pad;
+            for (int e = 0; e < d.w; ++e) {
+                const uint2 ent = nxt;
+                nxt = e + 1 < d.w ? __ldcs(blk + (int64_t)(e + 1) * 32 + lane) : pad;
+#pragma unroll
+                for (int t0 = 0; t0 < 16; t0 += kSpmm4BlkU) {
+                    float4 p[kSpmm4BlkU];
+#pragma unroll
+                    for (int u = 0; u < kSpmm4BlkU; ++u) {
+                        const int c = __shfl_sync(kFull, (int)ent.x, 2 * (t0 + u) + h);
+                        p[u] = gather4q(Xq, c, k);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kSpmm4BlkU; ++u) {
+                        const float v = __shfl_sync(kFull, __uint_as_float(ent.y), 2 * (t0 + u) + h);
+                        fma4(acc[t0 + u], v, p[u]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                tile[(2 * t + h) * 32 + 2 * q] = make_float2(acc[t].x, acc[t].y);
+                tile[(2 * t + h) * 32 + 2 * q + 1] = make_float2(acc[t].z, acc[t].w);
+            }
+            __syncwarp();
+#pragma unroll 1
+            for (int t0 = 0; t0 < nr; t0 += kSpmmEpi) {
+                uint32_t rid[kSpmmEpi];
+                RowPreK pre[kSpmmEpi];
+#pragma unroll
+                for (int u = 0; u < kSpmmEpi; ++u) {
+                    rid[u] = __shfl_sync(kFull, my_rid, (t0 + u) & 31);
+                    pre[u] = prefetch_row_k<MODE>(rid[u], t0 + u < nr, X, Y, k, j0);
+                }
+#pragma unroll
+                for (int u = 0; u < kSpmmEpi; ++u) {
+                    if (t0 + u < nr) {
+                        const float2 a = tile[(t0 + u) * 32 + lane];
+                        spmm_finish_pre<MODE>(E, sv, rid[u], a.x, a.y, pre[u], c0, k, lane, X, Y, seeds,
+                                              delta_k, redk, acc4);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// The k % 64 == 0 form of k_part_spmm (same launch geometry and sums).
+template <int MODE>
+__global__ void __launch_bounds__(kBlock, 2)
+k_part_spmm4(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__restrict__ Yout,
+             int k, const IterState *__restrict__ st, const int32_t *__restrict__ seeds,
+             const double *__restrict__ delta_k, double *__restrict__ redk)
+{
+    const float *X = Xin;
+    float *Y = Yout;
+    EpiK E;
+    E.c = 1.f;
+    E.dstart = 0;
+    if (st) {
+        const int par = st->parity;
+        X = st->buf[par];
+        Y = st->buf[par ^ 1];
+        E.c = (float)st->c;
+        E.dstart = st->dangling_start;
+    }
+    extern __shared__ float2 spmm_tile4[];   // per warp: 32 rows x 64 columns
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wid = blockIdx.x * kWarpsPerBlock + warp;
+    FSum acc4[4];
+    if (wid < pv.nwl) {
+        const Workload d = pv.wl[wid];
+        const uint2 *slab = pv.slab + d.slab;
+        const uint32_t *rows = pv.rows + d.rows;
+        if (d.major == 0)
+            spmm_rows4<MODE>(d, slab, rows, E, sv, X, Y, k, lane, seeds, delta_k, redk, acc4);
+        else
+            spmm_block4<MODE>(d, slab, rows, E, sv, X, Y, k, lane, seeds, delta_k, redk, acc4,
+                              spmm_tile4 + warp * 32 * 32);
+    }
+    if (MODE != EPI_RAW) {
+        __shared__ double sm[kWarpsPerBlock][4][32];
+        sm[warp][0][lane] = acc4[0].value(); sm[warp][1][lane] = acc4[1].value();
+        sm[warp][2][lane] = acc4[2].value(); sm[warp][3][lane] = acc4[3].value();
+        __syncthreads();
+        if (threadIdx.x < 128) {
+            const int qq = threadIdx.x >> 5, l = threadIdx.x & 31;
+            double a = 0.0;
+            for (int w = 0; w < kWarpsPerBlock; ++w) a += sm[w][qq][l];
+            const int j = 2 * l + (qq & 1);
+            if (j < k) {
+                double *o = redk + (int64_t)(pv.red_base + blockIdx.x) * 2 * k;
+                o[(qq >> 1) * k + j] = a;
+            }
+        }
+    }
+}
+
 // SpMM over one part.  Split rows: chunk partials (k floats per chunk slot)
 // in sv.partial, combined in chunk order by the last chunk.  Per-block
 // column sums for RWR into redk[(slot * 2 + q) * k + j] (q = 0: L1, 1: dangling).
@@ -1400,6 +1617,18 @@ void launch_part_spmm(int mode, const PartView &pv, const SplitView &sv, const f
         cudaFuncSetAttribute(k_part_spmm<EPI_RWR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_part_spmm<EPI_RWR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
+    }
+    static bool attr4 = false;
+    if (!attr4) {
+        cudaFuncSetAttribute(k_part_spmm4<EPI_RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_part_spmm4<EPI_RWR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr4 = true;
+    }
+    if (k % 64 == 0) {
+        if (mode == EPI_RAW) k_part_spmm4<EPI_RAW><<<g, b, smem, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
+        else k_part_spmm4<EPI_RWR><<<g, b, smem, s>>>(pv, sv, X, Y, k, st, seeds, delta_k, redk);
+        count_launches(1);
+        return;
     }
     const bool even = (k % 2) == 0;
     if (mode == EPI_RAW) {
