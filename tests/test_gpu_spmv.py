@@ -63,6 +63,9 @@ CONFIGS = [
     ("rmat14", dict(kernel=2)),                                # plain 8-warp kernel
     ("rmat14", dict(kernel=3, tile_width=2048)),               # TMA ring kernel
     ("rmat14", dict(kernel=1)),                                # staged x-slice kernel
+    ("rmat14", dict(kernel=4)),                                # slice-free persistent kernel
+    ("rmat14", dict(layout_rule=4, tile_width=2048)),          # storage rule chosen by the model
+    ("varied", dict(x_stage_cols=512, tile_width=1024)),       # slice on some parts only
     ("rmat14", dict(kernel=1, tile_width=2048, pattern_only=True)),
     ("varied", dict(kernel=1)),
     ("varied", dict(kernel=1, heavy_row=256, max_rows=-1)),
