@@ -598,6 +598,54 @@ __device__ __forceinline__ void do_workload(const Workload &d, const PartView &p
     }
 }
 
+// Up to four consecutive short column-major workloads of one claim unit
+// (one 32-row block each, at most kShortW entries per row) computed
+// together: each lane carries one row of each, so its four dependent
+// chains -- row entry and operands, slots, gathers, epilogue -- overlap
+// instead of running one after another (the row cap makes every ELL
+// workload a single block, so a warp otherwise has one chain per lane).
+// Each row's entries are summed in the same order as do_workload.
+// Measured (PageRank kernel per iteration): R-MAT scale 22 0.1552 vs 0.1655
+// ms, scale 24 0.7255 vs 0.7486 ms, scale 26 3.376 vs 3.468 ms; limits of
+// 8, 16 and 32 entries per row measured 0.1561, 0.1615 and 0.1619 ms at
+// scale 22.
+constexpr int kShortW = 4;
+
+__device__ __forceinline__ bool short_block(const Workload &d)
+{
+    return d.major == 1 && d.w > 0 && d.w <= kShortW && d.h <= 32;
+}
+
+template <int MODE, class G>
+__device__ __forceinline__ void do_short4(const Workload *dd, const PartView &pv, const SplitView &sv,
+                                          const G &g, const Epi &E, const float *__restrict__ x,
+                                          float *__restrict__ y, double2 *red, int lane, FSum &r0,
+                                          FSum &r1)
+{
+    RowPre pr[4];
+    float ac[4];
+    int wmax = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        pr[u] = prefetch_row<MODE>(E, pv.rows + dd[u].rows, lane, lane < dd[u].h, x, y);
+        ac[u] = 0.f;
+        wmax = max(wmax, (int)dd[u].w);
+    }
+    for (int e = 0; e < wmax; ++e) {
+        uint2 sl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const Slots<is_pattern(MODE)> slab{pv, dd[u].slab};
+            sl[u] = e < dd[u].w ? slab.ld((int64_t)e * 32 + lane) : make_uint2(0xffffffffu, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ac[u] = slot_fma_g(sl[u], g, ac[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (lane < dd[u].h) finish_row_pre<MODE>(E, sv, red, pr[u], ac[u], x, y, r0, r1);
+}
+
 template <int MODE>
 __device__ __forceinline__ void resolve_xy(const IterState *st, const float *&x, float *&y)
 {
@@ -685,8 +733,20 @@ k_part_staged(PartView pv, SplitView sv, const float *__restrict__ xin,
         u = __shfl_sync(kFull, u, 0);
         if (u >= (unsigned)pv.nunits) break;
         const int w0 = __ldg(pv.units + u), w1 = __ldg(pv.units + u + 1);
-        for (int w = w0; w < w1; ++w)
+        for (int w = w0; w < w1;) {
+            if (w + 3 < w1) {
+                Workload dd[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) dd[u] = pv.wl[w + u];
+                if (short_block(dd[0]) && short_block(dd[1]) && short_block(dd[2]) && short_block(dd[3])) {
+                    do_short4<MODE>(dd, pv, sv, g, E, x, y, red, lane, r0, r1);
+                    w += 4;
+                    continue;
+                }
+            }
             do_workload<MODE>(pv.wl[w], pv, sv, g, E, x, y, red, lane, r0, r1);
+            ++w;
+        }
     }
     if (lane == 0) {
         const unsigned done = atomicAdd(pv.sched + 1, 1u);
