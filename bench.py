@@ -724,19 +724,31 @@ def main():
 
     # ---- storage-rule ablation (the composite format's special cases):
     # every workload CSR-vector (rule 2), every workload ELL (rule 3), the
-    # paper's w >= h rule (0), against the default (1); model prediction
-    # beside the measured kernel time.  Skipped above 8M nodes (build time).
+    # paper's w >= h rule (0), against the default (1), and the rule the
+    # Algorithm 3 model picks per part (4) against the best forced one;
+    # model prediction beside the measured kernel time.  Skipped above 8M
+    # nodes (build time).
     ablation = None
     if n <= (1 << 23):
         ablation = {"default_rule1": {"kernel_ms": k_ms, "predicted_ms": info["predicted_ms"],
                                       "padded_slots": info["padded_slots"]}}
-        for rule, name in ((0, "paper_rule0"), (2, "all_csr_vector_rule2"), (3, "all_ell_rule3")):
+        for rule, name in ((0, "paper_rule0"), (2, "all_csr_vector_rule2"), (3, "all_ell_rule3"),
+                           (4, "model_chosen_rule4")):
             fa = spg.Format(rp, col, kind="pagerank", layout_rule=rule)
             fa.pagerank(DAMPING, tol=0.0, max_iter=3, like=like)
             ia = fa.info()
             ablation[name] = {"kernel_ms": float(fa.time_parts(mode=1, reps=20).sum()),
                               "predicted_ms": ia["predicted_ms"], "padded_slots": ia["padded_slots"]}
+            if rule == 4:
+                ablation[name]["rules_per_part"] = [fa.tile_info(p)["layout_rule"]
+                                                    for p in range(fa.nparts())]
             del fa
+        forced = {k: v["kernel_ms"] for k, v in ablation.items() if k != "model_chosen_rule4"}
+        best = min(forced, key=forced.get)
+        ablation["model_rule_vs_best_forced"] = {
+            "best_forced": best, "best_forced_ms": forced[best],
+            "model_rule_ms": ablation["model_chosen_rule4"]["kernel_ms"],
+            "ratio": ablation["model_chosen_rule4"]["kernel_ms"] / forced[best]}
         # claim order of the persistent kernel: the default (longest first
         # by dependent memory round trips) against the ranking order
         fo = spg.Format(rp, col, kind="pagerank", claim_order=1)
