@@ -169,8 +169,10 @@ typedef struct {
      * four (32 warps) for the fused power-iteration epilogues -- with every
      * gather through L1/L2.  2: plain 8-warp blocks, one workload per warp.
      * 3: option 1 with each warp's slots streamed into a shared-memory ring
-     * by TMA bulk copies.  Measured per PageRank iteration on GB300
-     * (kernel time, options 1 vs 4): R-MAT scale 22 0.170 vs 0.175 ms,
+     * by TMA bulk copies.  Options 1 and 4 also compute up to four
+     * consecutive short column-major workloads of a claim unit together.
+     * Measured per PageRank iteration on GB300 (kernel time, options 1 vs
+     * 4, before that change): R-MAT scale 22 0.170 vs 0.175 ms,
      * scale 24 0.757 vs 0.776 ms, scale 26 3.71 vs 3.77 ms; plain SpMV at
      * scale 22 0.157 vs 0.174 ms.  Scattered 4-byte gathers through L1 cost
      * one tag lookup per distinct line, which bounds the gather rate; the
@@ -329,8 +331,9 @@ spg_status spg_spmv_tile_coo(spg_handle h, const float *x_perm, float *y_perm, v
 
 /* Y = alpha * M X + beta * Y for k vectors: X (n x k) and Y (n x k) FP32,
  * row-major with leading dimensions ldx, ldy >= k, original row order.
- * One warp per workload, each lane two of every 64-column chunk; device
- * pointers only.  k in [1, 1024]. */
+ * One warp per workload; for k a multiple of 64 each half-warp gathers one
+ * stored entry's X row (16 bytes per lane), otherwise each lane takes two of
+ * every 64-column chunk; device pointers only.  k in [1, 1024]. */
 spg_status spg_spmm(spg_handle h, const float *X, int64_t ldx, float *Y, int64_t ldy, int k,
                     float alpha, float beta, void *stream);
 
