@@ -404,8 +404,9 @@ spg_status spg_unpack_slice(int64_t count, const int32_t *idx, const float *slic
  * the k restart nodes seeds[0..k) (host int32, original ids).  k == 1 runs
  * SpMV iterations; k > 1 runs them as one SpMM over the n x k block (R is
  * n x k row-major, original order); columns that converge keep iterating
- * until all have (their L1 stays below tol).  restart = 1 - c.
- * Kind PAGERANK. */
+ * until all have (their L1 stays below tol).  restart = 1 - c.  k in
+ * [1, 64] (one 64-column chunk of per-column sums); SPG_ERR_INVALID
+ * otherwise -- call again per group of 64 seeds.  Kind PAGERANK. */
 spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds, int k, double tol,
                    int max_iter, float *R, spg_iter_info *info, void *stream);
 

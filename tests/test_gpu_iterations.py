@@ -142,3 +142,12 @@ def test_rwr_batched_seeds(g14, k, opts):
     for j in list(range(0, k, max(1, k // 8))) + [k - 1]:
         r_star, _, _ = oracle.rwr(rp, col, int(seeds[j]), C, tol=1e-13, M=M)
         assert np.abs(R[:, j] - r_star).sum() <= 1e-6, j
+
+
+def test_rwr_refuses_more_than_64_seeds(g14):
+    rp, col, M, _ = g14
+    f = spg.Format(rp, col, kind="pagerank")
+    with pytest.raises(spg.SpgError) as e:
+        f.rwr(graphgen.pick_seeds(rp, 65, 4), restart=0.15, tol=1e-8, max_iter=10,
+              like=torch.empty(0, device=DEV))
+    assert e.value.status == -1

@@ -178,7 +178,8 @@ def test_baselines_match_oracle(which):
 
 
 @pytest.mark.parametrize("k,opts", [(64, dict(tile_width=2048)), (3, dict()), (130, dict(heavy_row=64)),
-                                    (64, dict(vec_width=64))])
+                                    (64, dict(vec_width=64)), (128, dict(heavy_row=64, tile_width=2048)),
+                                    (192, dict())])
 def test_spmm_matches_oracle(k, opts):
     rp, col = _graph("rmat12")
     n = rp.shape[0] - 1
