@@ -82,6 +82,9 @@ constexpr int kStagedMaxCols = 49152;
 // the columns past the slice are gathered through L1, and a 192 KB slice
 // (36 KB of L1 left) measured slower (R-MAT scale 24 PageRank iteration:
 // 0.749 ms with 24K columns, 0.872 ms with 48K, 0.776 ms with none).
+// Between 16K and 40K columns 24K is the fastest or within 1.1 % of it at
+// R-MAT scales 22 and 24, and the fastest at scale 26 (3.376 ms against
+// 3.440 with 28K and 3.412 with 32K).
 constexpr int kStagedDefaultCols = 24576;
 // Option 1 runs the slice kernel on a part only when the slice's columns
 // hold at least this share of the part's entries (R-MAT 22-26: 37-23 % in

@@ -3,6 +3,11 @@
 //
 //   lsu      global loads through L1/L2 (ld.global.nc), array L2-resident
 //            or not: every distinct 128-byte line costs an L1 tag lookup;
+//   lsu U    the same with U independent loads in flight per thread, to
+//            tell a throughput ceiling from too few loads in flight;
+//   tex U    1D texture fetches (tex1Dfetch over a linear buffer, the
+//            paper's texture-cache path), U in flight per thread, and an
+//            even mix of texture and global loads;
 //   rows256  a warp-wide coalesced 256-byte row per load (the SpMM gather);
 //   smem     loads from the block's own shared memory (96 KB slice);
 //   dsmem    loads from a thread-block cluster's distributed shared memory
@@ -44,6 +49,29 @@ __global__ void k_lsu(const float *__restrict__ x, const int *__restrict__ idx, 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += stride)
         acc += __ldg(x + (__ldg(idx + i) % span));
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+// U loads in flight per thread: thread t takes the U consecutive indices
+// of chunk t, t + T, ... (T threads; m a multiple of U).  PATH 0: global
+// loads, 1: texture fetches, 2: even u global, odd u texture.
+template <int U, int PATH>
+__global__ void k_gather_u(const float *__restrict__ x, cudaTextureObject_t tex, const int *__restrict__ idx,
+                           int64_t m, int span, float *out)
+{
+    float acc = 0.f;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * U; i0 + U <= m; i0 += nt * U) {
+        int c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) c[u] = __ldg(idx + i0 + u) % span;
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            v[u] = (PATH == 0 || (PATH == 2 && (u & 1) == 0)) ? __ldg(x + c[u]) : tex1Dfetch<float>(tex, c[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += v[u];
+    }
     out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
@@ -242,6 +270,49 @@ int main()
             ms = time_ms(e0, e1);
         }
         std::printf("lsu     span %9d floats: %.3e loads/s\n", span, m / (ms * 1e-3));
+    }
+    // loads in flight per thread, global and texture paths
+    int tex_max = 0;
+    CK(cudaDeviceGetAttribute(&tex_max, cudaDevAttrMaxTexture1DLinearWidth, 0));
+    for (int span : {1 << 22, 1 << 24, 1 << 27}) {
+        cudaTextureObject_t tex = 0;
+        const bool have_tex = span <= tex_max;
+        if (have_tex) {
+            cudaResourceDesc rd = {};
+            rd.resType = cudaResourceTypeLinear;
+            rd.res.linear.devPtr = x;
+            rd.res.linear.desc = cudaCreateChannelDesc<float>();
+            rd.res.linear.sizeInBytes = (size_t)span * sizeof(float);
+            cudaTextureDesc td = {};
+            td.readMode = cudaReadModeElementType;
+            CK(cudaCreateTextureObject(&tex, &rd, &td, nullptr));
+        }
+        for (int path = 0; path < (have_tex ? 3 : 1); ++path) {
+            for (int u : {1, 4, 8}) {
+                float ms = 0.f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    CK(cudaEventRecord(e0));
+                    const dim3 g(sms * 8), b(256);
+                    if (path == 0 && u == 1) k_gather_u<1, 0><<<g, b>>>(x, tex, idx, m, span, out);
+                    if (path == 0 && u == 4) k_gather_u<4, 0><<<g, b>>>(x, tex, idx, m, span, out);
+                    if (path == 0 && u == 8) k_gather_u<8, 0><<<g, b>>>(x, tex, idx, m, span, out);
+                    if (path == 1 && u == 1) k_gather_u<1, 1><<<g, b>>>(x, tex, idx, m, span, out);
+                    if (path == 1 && u == 4) k_gather_u<4, 1><<<g, b>>>(x, tex, idx, m, span, out);
+                    if (path == 1 && u == 8) k_gather_u<8, 1><<<g, b>>>(x, tex, idx, m, span, out);
+                    if (path == 2 && u == 1) k_gather_u<2, 2><<<g, b>>>(x, tex, idx, m, span, out);
+                    if (path == 2 && u == 4) k_gather_u<4, 2><<<g, b>>>(x, tex, idx, m, span, out);
+                    if (path == 2 && u == 8) k_gather_u<8, 2><<<g, b>>>(x, tex, idx, m, span, out);
+                    CK(cudaEventRecord(e1));
+                    CK(cudaEventSynchronize(e1));
+                    CK(cudaGetLastError());
+                    ms = time_ms(e0, e1);
+                }
+                static const char *name[3] = {"lsu", "tex", "lsu+tex"};
+                std::printf("%-7s span %9d floats, %d in flight per thread: %.3e loads/s\n", name[path], span,
+                            path == 2 && u == 1 ? 2 : u, m / (ms * 1e-3));
+            }
+        }
+        if (have_tex) CK(cudaDestroyTextureObject(tex));
     }
     // 256-byte rows (an n x 64 FP32 block): 2^18 rows (64 MB, fits L2) and
     // 2^21 rows (512 MB), 8 or 16 rows in flight per warp
