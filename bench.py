@@ -274,7 +274,7 @@ def run_secondary(args):
         e2e_v = flops * 3 / (time.perf_counter() - t1) / 1e9
         extra = {"roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
                               "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak,
-                              "traffic": None, "kernel": "k_part_spmm<EPI_RWR> + check per iteration"},
+                              "traffic": None, "kernel": "k_part_spmm4<EPI_RWR> + check per iteration"},
                  "e2e": {"value": e2e_v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                          "d2h_bytes_per_step": 4 * 64 * n}}
         value = flops / (ms * 1e-3) / 1e9

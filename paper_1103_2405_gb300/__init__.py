@@ -69,7 +69,7 @@ class _TileInfo(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in
                 ("col_begin", "col_end", "heavy", "wl", "nvirt", "nwl", "nnz")] + \
                [("predicted_ms", ctypes.c_double), ("layout_rule", ctypes.c_int64),
-                ("slice_share", ctypes.c_double)]
+                ("slice_share", ctypes.c_double), ("nunits", ctypes.c_int64)]
 
 
 # Every symbol include/spg.h declares.
@@ -494,7 +494,7 @@ class BatchFormat:
 
     def __init__(self, graphs, heavy_row=-1, layout_rule=1, max_warps=0, x_stage_cols=0,
                  slab_prefetch=0, loop_mode=0, max_rows=0, kernel=0, host_only=False, table=None,
-                 claim_order=0, stream=None):
+                 claim_order=0, keep_plan=False, unit_slots=0, stream=None):
         L = lib()
         keep = []
         arr = (_Csr * len(graphs))()
@@ -511,6 +511,8 @@ class BatchFormat:
                      int(x_stage_cols), int(slab_prefetch), int(loop_mode), int(max_rows),
                      int(kernel), 0)
         opts.claim_order = int(claim_order)
+        opts.keep_plan = int(bool(keep_plan))
+        opts.unit_slots = int(unit_slots)
         self._h = ctypes.c_void_p(None)
         _check(L.spg_build_batch(ctypes.cast(arr, ctypes.c_void_p), len(graphs), ctypes.byref(opts),
                                  _stream(stream), ctypes.byref(self._h)))
@@ -534,6 +536,18 @@ class BatchFormat:
         i = _Info()
         _check(lib().spg_format_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in _Info._fields_}
+
+    tile_info = Format.tile_info
+    export_plan = Format.export_plan
+    perm = Format.perm
+
+    def export_entries(self):
+        nnz = self.info()["nnz"]
+        r = np.empty(nnz, np.int64)
+        c = np.empty(nnz, np.int32)
+        v = np.empty(nnz, np.float32)
+        _check(lib().spg_format_export_entries(self._h, _ptr(r)[0], _ptr(c)[0], _ptr(v)[0]))
+        return r, c, v
 
     def pagerank(self, damping=0.85, tol=1e-8, max_iter=1000, out=None, like=None, stream=None):
         """Concatenated PageRank vectors and one info dict per graph."""

@@ -182,6 +182,16 @@ static inline int64_t claim_cost(const Workload &d)
 // units are then runs of consecutive workloads whose cost reaches
 // unit_slots, so that one atomic on the work counter covers several small
 // workloads while a large one stays alone.
+//
+// Block-diagonal unions (BuildParams::segment_order): the workloads are then
+// stored segment by segment -- the segment (graph) of a workload's first row,
+// stable, so the longest-first order holds within a segment, row-free
+// workloads last -- and claim units end at segment boundaries.  The per-
+// segment degree order keeps every segment's rows and columns at its own
+// positions, so the warps running at any moment work on a few graphs and
+// share their x and y lines in L1 and L2 (512 Chung-Lu graphs, PageRank
+// iteration with the persistent 8-warp kernel: 0.625 ms against 0.677 ms in
+// the longest-first order over all graphs).
 static void order_and_group(Layout &L, const BuildParams &prm)
 {
     if (prm.claim_order == 0 && !L.wl.empty()) {
@@ -196,11 +206,40 @@ static void order_and_group(Layout &L, const BuildParams &prm)
             for (int64_t j = 0; j < ph.nwl_total; ++j) b[j] = key[(size_t)j].second;
         }
     }
+    const bool grouped = prm.segment_order && prm.nseg > 0 && L.parts.size() == 1 && !L.wl.empty();
+    std::vector<int32_t> wgroup;   // segment of each workload of part 0 (nseg: row-free)
+    if (grouped) {
+        const int64_t *so = prm.seg_off;
+        const int32_t G = (int32_t)prm.nseg;
+        const PartHost &ph = L.parts[0];
+        auto b = L.wl.begin() + ph.wl_off;
+        std::vector<std::pair<int32_t, Workload>> key((size_t)ph.nwl_total);
+        for (int64_t j = 0; j < ph.nwl_total; ++j) {
+            int32_t g = G;
+            if (b[j].w > 0) {
+                uint32_t e = L.rows[(size_t)b[j].rows];
+                if (e & kRowSplit) e = L.split[(size_t)L.slot_owner[(size_t)(e & ~kRowSplit)]].row;
+                const int64_t r = (int64_t)(e & kRowIdMask);
+                g = (int32_t)(std::upper_bound(so, so + G + 1, r) - so) - 1;
+            }
+            key[(size_t)j] = {g, b[j]};
+        }
+        std::stable_sort(key.begin(), key.end(),
+                         [](const std::pair<int32_t, Workload> &a, const std::pair<int32_t, Workload> &c) {
+                             return a.first < c.first;
+                         });
+        wgroup.resize((size_t)ph.nwl_total);
+        for (int64_t j = 0; j < ph.nwl_total; ++j) {
+            b[j] = key[(size_t)j].second;
+            wgroup[(size_t)j] = key[(size_t)j].first;
+        }
+    }
     L.units.clear();
     for (PartHost &ph : L.parts) {
         ph.unit_off = (int64_t)L.units.size();
         int64_t acc = 0;
         for (int64_t j = 0; j < ph.nwl_total; ++j) {
+            if (grouped && j > 0 && wgroup[(size_t)j] != wgroup[(size_t)j - 1]) acc = 0;
             if (acc == 0) L.units.push_back((int32_t)j);
             acc += L.wl.empty() ? 1 : claim_cost(L.wl[(size_t)(ph.wl_off + j)]);
             if (prm.unit_slots <= 1 || acc >= prm.unit_slots) acc = 0;

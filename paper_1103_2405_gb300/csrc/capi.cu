@@ -620,6 +620,7 @@ extern "C" spg_status spg_tile_info(spg_handle h, int64_t part, spg_tile_info_t 
     info->predicted_ms = p.predicted_s * 1e3;
     info->layout_rule = p.rule;
     info->slice_share = p.slice_share;
+    info->nunits = p.nunits;
     return SPG_OK;
 }
 
@@ -1781,6 +1782,7 @@ extern "C" spg_status spg_build_batch(const spg_csr *graphs, int count,
         prm.stage_cols = resolve_stage_cols(o);
         prm.seg_off = h->goff.data();
         prm.nseg = count;
+        prm.segment_order = prm.claim_order == 0;   // longest first within each graph, graph by graph
         std::string err;
         if (!build_layout(src, prm, h->fwd, err)) return fail(SPG_ERR_INVALID, err);
         if (!h->host_only) {

@@ -48,6 +48,9 @@ struct BuildParams {
     // columns of the shared-memory x slice the kernel would stage per part
     // (for PartHost::slice_share; 0 = none)
     int64_t stage_cols = 0;
+    // block-diagonal unions (nseg > 0) of one part: store (and claim) the
+    // part's workloads segment by segment, claim units within a segment
+    bool segment_order = false;
     // claim units of the persistent kernels: consecutive workloads grouped
     // until their cost (padded slots + 4 per row) reaches this; <= 1 = one
     // workload per unit

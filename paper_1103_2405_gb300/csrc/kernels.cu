@@ -1412,8 +1412,26 @@ __device__ __forceinline__ void spmm_block(const Workload &d, const uint2 *__res
 #ifndef SPG_SPMM4_BLKU
 #define SPG_SPMM4_BLKU 4
 #endif
+// Row pairs of a block summed per pass: two passes of 16 rows (the block's
+// slots read twice) hold half the sums in registers and spill less than one
+// pass of 32 (RWR k = 64 at R-MAT scale 22: 2.553 ms per iteration against
+// 2.622 with one pass and 2.806 with four); a third resident block per SM
+// (80 registers, all of the carve-out to shared memory) measured 3.40-4.24 ms.
+#ifndef SPG_SPMM4_PASS
+#define SPG_SPMM4_PASS 8
+#endif
+#ifndef SPG_SPMM4_MINB
+#define SPG_SPMM4_MINB 2
+#endif
 constexpr int kSpmm4RowU = SPG_SPMM4_ROWU;   // entry pairs gathered together, row-major path
 constexpr int kSpmm4BlkU = SPG_SPMM4_BLKU;   // row pairs gathered together per step, block path
+constexpr int kSpmm4Pass = SPG_SPMM4_PASS;   // row pairs of a 32-row block summed per pass
+constexpr int kSpmm4MinB = SPG_SPMM4_MINB;   // resident blocks per SM (register budget)
+#ifndef SPG_SPMM4_EPI
+#define SPG_SPMM4_EPI 4
+#endif
+constexpr int kSpmm4Epi = SPG_SPMM4_EPI;     // block rows whose epilogue operands are fetched together
+static_assert(16 % kSpmm4Pass == 0 && kSpmm4Pass % kSpmm4BlkU == 0, "SpMM pass shape");
 
 __device__ __forceinline__ float4 gather4q(const float *__restrict__ Xq, int c, int k)
 {
@@ -1485,10 +1503,10 @@ __device__ __forceinline__ void spmm_rows4(const Workload &d, const uint2 *__res
     }
 }
 
-// Column-major block of 32 rows: half h sums rows 2t + h (t = 0..15) for its
-// column quad, step by step (the same order of the row's entries as the
-// float2 form), then writes the sums to the warp's tile in the float2-per-
-// lane layout for the epilogue.
+// Column-major block of 32 rows: half h sums rows 2t + h for its column
+// quad, kSpmm4Pass row pairs t per pass over the block's slots, step by step
+// (the same order of the row's entries as the float2 form), then writes the
+// sums to the warp's tile in the float2-per-lane layout for the epilogue.
 template <int MODE>
 __device__ __forceinline__ void spmm_block4(const Workload &d, const uint2 *__restrict__ slab,
                                             const uint32_t *__restrict__ rows, const EpiK &E,
@@ -1507,60 +1525,65 @@ __device__ __forceinline__ void spmm_block4(const Workload &d, const uint2 *__re
         for (int c0 = 0; c0 < k; c0 += 64) {
             const float *Xq = X + c0 + 4 * q;
             const int j0 = c0 + 2 * lane;
-            float4 acc[16];
-#pragma unroll
-            for (int t = 0; t < 16; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-            uint2 nxt = d.w > 0 ? __ldcs(blk + lane) : pad;
-            for (int e = 0; e < d.w; ++e) {
-                const uint2 ent = nxt;
-                nxt = e + 1 < d.w ? __ldcs(blk + (int64_t)(e + 1) * 32 + lane) : pad;
-#pragma unroll
-                for (int t0 = 0; t0 < 16; t0 += kSpmm4BlkU) {
-                    float4 p[kSpmm4BlkU];
-#pragma unroll
-                    for (int u = 0; u < kSpmm4BlkU; ++u) {
-                        const int c = __shfl_sync(kFull, (int)ent.x, 2 * (t0 + u) + h);
-                        p[u] = gather4q(Xq, c, k);
-                    }
-#pragma unroll
-                    for (int u = 0; u < kSpmm4BlkU; ++u) {
-                        const float v = __shfl_sync(kFull, __uint_as_float(ent.y), 2 * (t0 + u) + h);
-                        fma4(acc[t0 + u], v, p[u]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                tile[(2 * t + h) * 32 + 2 * q] = make_float2(acc[t].x, acc[t].y);
-                tile[(2 * t + h) * 32 + 2 * q + 1] = make_float2(acc[t].z, acc[t].w);
-            }
-            __syncwarp();
 #pragma unroll 1
-            for (int t0 = 0; t0 < nr; t0 += kSpmmEpi) {
-                uint32_t rid[kSpmmEpi];
-                RowPreK pre[kSpmmEpi];
+            for (int tp = 0; tp < 16 && 2 * tp < nr; tp += kSpmm4Pass) {
+                // pass over row pairs tp .. tp + kSpmm4Pass - 1 (rows 2 tp .. 2 tp + 2 kSpmm4Pass - 1)
+                float4 acc[kSpmm4Pass];
 #pragma unroll
-                for (int u = 0; u < kSpmmEpi; ++u) {
-                    rid[u] = __shfl_sync(kFull, my_rid, (t0 + u) & 31);
-                    pre[u] = prefetch_row_k<MODE>(rid[u], t0 + u < nr, X, Y, k, j0);
-                }
+                for (int t = 0; t < kSpmm4Pass; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                uint2 nxt = d.w > 0 ? __ldcs(blk + lane) : pad;
+                for (int e = 0; e < d.w; ++e) {
+                    const uint2 ent = nxt;
+                    nxt = e + 1 < d.w ? __ldcs(blk + (int64_t)(e + 1) * 32 + lane) : pad;
 #pragma unroll
-                for (int u = 0; u < kSpmmEpi; ++u) {
-                    if (t0 + u < nr) {
-                        const float2 a = tile[(t0 + u) * 32 + lane];
-                        spmm_finish_pre<MODE>(E, sv, rid[u], a.x, a.y, pre[u], c0, k, lane, X, Y, seeds,
-                                              delta_k, redk, acc4);
+                    for (int t0 = 0; t0 < kSpmm4Pass; t0 += kSpmm4BlkU) {
+                        float4 p[kSpmm4BlkU];
+#pragma unroll
+                        for (int u = 0; u < kSpmm4BlkU; ++u) {
+                            const int c = __shfl_sync(kFull, (int)ent.x, 2 * (tp + t0 + u) + h);
+                            p[u] = gather4q(Xq, c, k);
+                        }
+#pragma unroll
+                        for (int u = 0; u < kSpmm4BlkU; ++u) {
+                            const float v = __shfl_sync(kFull, __uint_as_float(ent.y), 2 * (tp + t0 + u) + h);
+                            fma4(acc[t0 + u], v, p[u]);
+                        }
                     }
                 }
+#pragma unroll
+                for (int t = 0; t < kSpmm4Pass; ++t) {
+                    tile[(2 * (tp + t) + h) * 32 + 2 * q] = make_float2(acc[t].x, acc[t].y);
+                    tile[(2 * (tp + t) + h) * 32 + 2 * q + 1] = make_float2(acc[t].z, acc[t].w);
+                }
+                __syncwarp();
+                const int rend = min(nr, 2 * (tp + kSpmm4Pass));
+#pragma unroll 1
+                for (int t0 = 2 * tp; t0 < rend; t0 += kSpmm4Epi) {
+                    uint32_t rid[kSpmm4Epi];
+                    RowPreK pre[kSpmm4Epi];
+#pragma unroll
+                    for (int u = 0; u < kSpmm4Epi; ++u) {
+                        rid[u] = __shfl_sync(kFull, my_rid, (t0 + u) & 31);
+                        pre[u] = prefetch_row_k<MODE>(rid[u], t0 + u < rend, X, Y, k, j0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kSpmm4Epi; ++u) {
+                        if (t0 + u < rend) {
+                            const float2 a = tile[(t0 + u) * 32 + lane];
+                            spmm_finish_pre<MODE>(E, sv, rid[u], a.x, a.y, pre[u], c0, k, lane, X, Y, seeds,
+                                                  delta_k, redk, acc4);
+                        }
+                    }
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
 }
 
 // The k % 64 == 0 form of k_part_spmm (same launch geometry and sums).
 template <int MODE>
-__global__ void __launch_bounds__(kBlock, 2)
+__global__ void __launch_bounds__(kBlock, kSpmm4MinB)
 k_part_spmm4(PartView pv, SplitView sv, const float *__restrict__ Xin, float *__restrict__ Yout,
              int k, const IterState *__restrict__ st, const int32_t *__restrict__ seeds,
              const double *__restrict__ delta_k, double *__restrict__ redk)
@@ -1682,6 +1705,12 @@ void launch_part_spmm(int mode, const PartView &pv, const SplitView &sv, const f
     if (!attr4) {
         cudaFuncSetAttribute(k_part_spmm4<EPI_RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_part_spmm4<EPI_RWR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (kSpmm4MinB > 2) {   // more than two 72 KB blocks per SM: all of the carve-out to shared memory
+            cudaFuncSetAttribute(k_part_spmm4<EPI_RAW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+            cudaFuncSetAttribute(k_part_spmm4<EPI_RWR>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        }
         attr4 = true;
     }
     if (k % 64 == 0) {

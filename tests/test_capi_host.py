@@ -188,6 +188,26 @@ def test_batch_host_build_orders_within_each_graph(spg):
         assert np.array_equal(seg, inv_ref)       # Solution 2 order within each graph
 
 
+def test_batch_claim_order_only_reorders(spg):
+    # graph-by-graph claim order (claim_order 0) against the ranking order
+    # (claim_order 1): same plan, same stored entries; claim units never
+    # span two graphs, so there are at least as many
+    sizes = [40, 300, 77, 1000, 2500, 60, 90, 700, 1500, 33, 5000, 128]
+    graphs = [graphgen.chung_lu(n, 12 * n, 2.3, n / 4, seed=50 + i) for i, n in enumerate(sizes)]
+    b = spg.BatchFormat(graphs, host_only=True, max_warps=64, keep_plan=True)
+    ref = spg.BatchFormat(graphs, host_only=True, max_warps=64, keep_plan=True, claim_order=1)
+    pa, pb = b.export_plan(0), ref.export_plan(0)
+    for k in ("rank_row", "rank_chunk", "rank_len", "wl_first", "wl_h", "wl_w", "wl_major"):
+        assert np.array_equal(pa[k], pb[k]), k
+    ea, eb = b.export_entries(), ref.export_entries()
+    oa, ob = np.lexsort((ea[1], ea[0])), np.lexsort((eb[1], eb[0]))
+    for x, y in zip(ea, eb):
+        assert np.array_equal(x[oa], y[ob])
+    assert b.tile_info(0)["nunits"] >= ref.tile_info(0)["nunits"]
+    one = spg.BatchFormat(graphs, host_only=True, max_warps=64, unit_slots=1)
+    assert one.tile_info(0)["nunits"] == one.tile_info(0)["nwl"] + -(-one.info()["zero_rows"] // 1024)
+
+
 def test_bad_table_rejected(spg):
     fd, path = tempfile.mkstemp(suffix=".txt")
     with os.fdopen(fd, "w") as f:

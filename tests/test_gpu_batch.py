@@ -22,7 +22,8 @@ def _batch(count, lo, hi, seed=1000):
     return graphs
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(x_stage_cols=-1, heavy_row=0)])
+@pytest.mark.parametrize("opts", [dict(), dict(x_stage_cols=-1, heavy_row=0),
+                                  dict(claim_order=1), dict(kernel=1, unit_slots=1)])
 def test_batch_pagerank_matches_oracle(opts):
     graphs = _batch(24, 6, 12)
     graphs.append((np.zeros(4, np.int64), np.zeros(0, np.int32)))    # edgeless graph
@@ -48,3 +49,14 @@ def test_batch_fixed_iterations_equal_single_graph_runs():
     for (rp, col), pg in zip(graphs, b.split(p.cpu().numpy())):
         ref, _, _ = oracle.pagerank(rp, col, 0.85, tol=0.0, max_iter=7)
         assert np.abs(pg - ref).sum() <= 1e-6
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(x_stage_cols=-1)])
+def test_claim_orders_agree_bit_for_bit(opts):
+    # graph-by-graph and ranking claim orders, persistent and plain kernels:
+    # every row is summed in the same order, so the iterates are identical
+    graphs = _batch(40, 6, 12, seed=31)
+    like = torch.empty(0, device=DEV)
+    p, _ = spg.BatchFormat(graphs, **opts).pagerank(0.85, tol=0.0, max_iter=9, like=like)
+    q, _ = spg.BatchFormat(graphs, claim_order=1).pagerank(0.85, tol=0.0, max_iter=9, like=like)
+    assert torch.equal(p, q)
