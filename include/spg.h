@@ -17,9 +17,16 @@
  *    ABI.  SPG_NOT_CONVERGED is a positive warning: outputs are written.
  *  - Vectors are FP32, in ORIGINAL node order, and may be device pointers or
  *    host pointers (pageable or pinned); the library detects which with
- *    cudaPointerGetAttributes and stages host data through its own device
- *    workspace.  The caller owns every vector; the library keeps no caller
- *    pointer after a call returns.
+ *    cudaPointerGetAttributes.  Pinned (page-locked, mapped) host vectors
+ *    are read (x of spg_spmv, p0 of spg_pagerank, g of spg_rwr_adjoint) and
+ *    written (y of spg_spmv, the results of spg_pagerank, spg_rwr with
+ *    k = 1, spg_pagerank_ranks and spg_batch_pagerank) by the permutation
+ *    kernels directly over the host link, in order, without a staging copy:
+ *    the reordering between node order and the format's position order and
+ *    the transfer are one pass.  Pageable host vectors, and the other host
+ *    vectors, are staged through the library's own device workspace.  The caller owns
+ *    every vector; the library keeps no caller pointer after a call
+ *    returns.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls on
  *    device vectors are asynchronous on that stream; calls that take or
  *    return host vectors, and calls that report iteration counts, synchronise

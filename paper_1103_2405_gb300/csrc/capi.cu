@@ -834,6 +834,19 @@ static spg_status ensure_vectors(spg_handle h, int64_t N)
     return SPG_OK;
 }
 
+// Device alias of mapped (pinned) host memory -- kernels read and write it
+// straight over the host link -- or nullptr (device or pageable memory).
+static void *mapped_host(const void *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Input vector on the device: the caller's pointer or a staged copy.
 static spg_status device_in(spg_handle h, const float *p, int64_t count, const float **out,
                             cudaStream_t s)
@@ -842,6 +855,44 @@ static spg_status device_in(spg_handle h, const float *p, int64_t count, const f
     CK(h->stage_in.ensure((size_t)count));
     CK(cudaMemcpyAsync(h->stage_in.p, p, count * sizeof(float), cudaMemcpyHostToDevice, s));
     *out = h->stage_in.p;
+    return SPG_OK;
+}
+
+// A caller's vector of n floats (original order; device, mapped host or
+// pageable host memory) into position order: dst[pi(j)] = src[j], times
+// d[pi(j)] when d is given.  Device memory is gathered by position; mapped
+// host memory is read once, in order, over the host link (no staging
+// copy); pageable memory is staged, then gathered.
+static spg_status permute_in(spg_handle h, const Layout &L, const float *src, int64_t n,
+                             const float *d, float *dst, cudaStream_t s)
+{
+    if (const float *a = is_device_ptr(src) ? nullptr : (const float *)mapped_host(src)) {
+        launch_permute_in(n, L.d_perm, a, d, dst, s);
+        return SPG_OK;
+    }
+    const float *sd;
+    spg_status st = device_in(h, src, n, &sd, s);
+    if (st != SPG_OK) return st;
+    if (d) launch_gather_scaled(n, L.d_inv, sd, d, dst, s);
+    else launch_gather(n, L.d_inv, sd, dst, s);
+    return SPG_OK;
+}
+
+// Where an output kernel writes a caller's vector of n floats: its device
+// memory, the device alias of its mapped host memory (written in order
+// over the host link, no staging copy), or the staging buffer for pageable
+// memory (*staged set: copy it out after the kernel; keep_old: the kernel
+// reads the old values too, copy them in first).
+static spg_status out_target(spg_handle h, float *p, int64_t n, bool keep_old, float **od, bool *staged,
+                             cudaStream_t s)
+{
+    *staged = false;
+    if (is_device_ptr(p)) { *od = p; return SPG_OK; }
+    if (float *a = (float *)mapped_host(p)) { *od = a; return SPG_OK; }
+    CK(h->stage_out.ensure((size_t)n));
+    *od = h->stage_out.p;
+    *staged = true;
+    if (keep_old) CK(cudaMemcpyAsync(*od, p, n * sizeof(float), cudaMemcpyHostToDevice, s));
     return SPG_OK;
 }
 
@@ -923,24 +974,16 @@ extern "C" spg_status spg_spmv(spg_handle h, const float *x, float *y, float alp
     const int64_t N = h->fwd.n;
     spg_status st = ensure_vectors(h, N);
     if (st != SPG_OK) return st;
-    const float *xd;
-    if ((st = device_in(h, x, N, &xd, s)) != SPG_OK) return st;
-    const bool y_host = !is_device_ptr(y);
-    float *yd = y;
-    if (y_host) {
-        CK(h->stage_out.ensure((size_t)N));
-        yd = h->stage_out.p;
-        if (beta != 0.f) CK(cudaMemcpyAsync(yd, y, N * sizeof(float), cudaMemcpyHostToDevice, s));
-    }
-    if (h->fwd.pattern) launch_gather_scaled(N, h->fwd.d_inv, xd, h->fwd.d_inv_deg, h->x.p, s);
-    else launch_gather(N, h->fwd.d_inv, xd, h->x.p, s);
+    if ((st = permute_in(h, h->fwd, x, N, h->fwd.pattern ? h->fwd.d_inv_deg : nullptr, h->x.p, s)) != SPG_OK)
+        return st;
+    float *yd;
+    bool staged;
+    if ((st = out_target(h, y, N, beta != 0.f, &yd, &staged, s)) != SPG_OK) return st;
     launch_parts(h, EPI_RAW, h->x.p, h->y.p, nullptr, nullptr, s);
-    launch_scatter_axpby(N, h->fwd.d_inv, h->y.p, yd, alpha, beta, s);
+    launch_unpermute_axpby(N, h->fwd.d_perm, h->y.p, yd, alpha, beta, s);
     CK(cudaGetLastError());
-    if (y_host) {
-        CK(cudaMemcpyAsync(y, yd, N * sizeof(float), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-    }
+    if (staged) CK(cudaMemcpyAsync(y, yd, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (!is_device_ptr(y)) CK(cudaStreamSynchronize(s));
     return SPG_OK;
 }
 
@@ -1145,9 +1188,7 @@ extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int 
     }
     if ((st = upload_state(h, hs, s)) != SPG_OK) return st;
     if (p0) {
-        const float *pd;
-        if ((st = device_in(h, p0, N, &pd, s)) != SPG_OK) return st;
-        launch_gather(N, h->fwd.d_inv, pd, h->x.p, s);
+        if ((st = permute_in(h, h->fwd, p0, N, nullptr, h->x.p, s)) != SPG_OK) return st;
     } else {
         launch_fill(N, (float)(1.0 / (double)N), h->x.p, s);
     }
@@ -1162,11 +1203,11 @@ extern "C" spg_status spg_pagerank(spg_handle h, float damping, double tol, int 
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
     if ((st = launch_loop(h, g, max_iter, s)) != SPG_OK) return st;
-    const bool out_host = !is_device_ptr(p_out);
-    float *od = p_out;
-    if (out_host) { CK(h->stage_out.ensure((size_t)N)); od = h->stage_out.p; }
-    launch_scatter_state(N, h->fwd.d_inv, h->d_state, od, nullptr, 0, s);
-    if (out_host) CK(cudaMemcpyAsync(p_out, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    float *od;
+    bool staged;
+    if ((st = out_target(h, p_out, N, false, &od, &staged, s)) != SPG_OK) return st;
+    launch_unpermute_state(N, h->fwd.d_perm, h->d_state, od, nullptr, 0, s);
+    if (staged) CK(cudaMemcpyAsync(p_out, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if ((st = finish_loop(h, g, max_iter, &hs, info)) != SPG_OK) return st;
     return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
@@ -1197,7 +1238,7 @@ extern "C" spg_status spg_hits(spg_handle h, int norm, double tol, int max_iter,
     if ((st = run_loop(h, g, max_iter, &hs, info, s)) != SPG_OK) return st;
     // normalised iterate into [auth; hub] (original order)
     CK(h->stage_out.ensure((size_t)N));
-    launch_scatter_state(N, h->fwd.d_inv, h->d_state, h->stage_out.p, h->d_row_half, 1, s);
+    launch_unpermute_state(N, h->fwd.d_perm, h->d_state, h->stage_out.p, h->d_row_half, 1, s);
     const cudaMemcpyKind ka = is_device_ptr(auth) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const cudaMemcpyKind kh = is_device_ptr(hub) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CK(cudaMemcpyAsync(auth, h->stage_out.p, n * sizeof(float), ka, s));
@@ -1246,11 +1287,11 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
         if (st != SPG_OK) return st;
         CK(cudaGetLastError());
         if ((st = run_loop(h, g, max_iter, &hs, info, s)) != SPG_OK) return st;
-        const bool out_host = !is_device_ptr(R);
-        float *od = R;
-        if (out_host) { CK(h->stage_out.ensure((size_t)N)); od = h->stage_out.p; }
-        launch_scatter_state(N, L.d_inv, h->d_state, od, nullptr, 0, s);
-        if (out_host) CK(cudaMemcpyAsync(R, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+        float *od;
+        bool staged;
+        if ((st = out_target(h, R, N, false, &od, &staged, s)) != SPG_OK) return st;
+        launch_unpermute_state(N, L.d_perm, h->d_state, od, nullptr, 0, s);
+        if (staged) CK(cudaMemcpyAsync(R, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
     }
@@ -1390,11 +1431,11 @@ extern "C" spg_status spg_pagerank_ranks(const spg_handle *ranks, int P, float d
     CK(cudaGetLastError());
     spg_status st = run_loop(h0, &lg, max_iter, &hs, info, s);
     if (st != SPG_OK) return st;
-    const bool out_host = !is_device_ptr(p_out);
-    float *od = p_out;
-    if (out_host) { CK(h0->stage_out.ensure((size_t)N)); od = h0->stage_out.p; }
-    launch_scatter_state(N, h0->fwd.d_inv, h0->d_state, od, nullptr, 0, s);
-    if (out_host) CK(cudaMemcpyAsync(p_out, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    float *od;
+    bool staged;
+    if ((st = out_target(h0, p_out, N, false, &od, &staged, s)) != SPG_OK) return st;
+    launch_unpermute_state(N, h0->fwd.d_perm, h0->d_state, od, nullptr, 0, s);
+    if (staged) CK(cudaMemcpyAsync(p_out, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
 }
@@ -1669,9 +1710,7 @@ extern "C" spg_status spg_rwr_adjoint(spg_handle h, float restart, int32_t seed,
     CK(h->red.ensure((size_t)std::max(1, nred)));
     CK(h->aux.ensure((size_t)n));
     // g into the transposed layout's order; lambda(0) = g
-    const float *gd;
-    if ((st = device_in(h, g, n, &gd, s)) != SPG_OK) return st;
-    launch_gather(n, Lb.d_inv, gd, h->aux.p, s);
+    if ((st = permute_in(h, Lb, g, n, nullptr, h->aux.p, s)) != SPG_OK) return st;
     CK(cudaMemcpyAsync(h->x.p, h->aux.p, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
     const double c = 1.0 - (double)restart;
     IterState hs = make_state(h, c, tol, max_iter, n, h->x.p, h->y.p);
@@ -1689,7 +1728,7 @@ extern "C" spg_status spg_rwr_adjoint(spg_handle h, float restart, int32_t seed,
     const bool lam_host = lambda && !is_device_ptr(lambda);
     CK(h->stage_out.ensure((size_t)n));
     float *lam_d = (lambda && !lam_host) ? lambda : h->stage_out.p;
-    launch_scatter_state(n, Lb.d_inv, h->d_state, lam_d, nullptr, 0, s);
+    launch_unpermute_state(n, Lb.d_perm, h->d_state, lam_d, nullptr, 0, s);
     if (lam_host) CK(cudaMemcpyAsync(lambda, lam_d, n * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (dtheta) {
         const float *rd = r;
@@ -1878,11 +1917,11 @@ extern "C" spg_status spg_batch_pagerank(spg_handle h, float damping, double tol
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
     if ((st = run_loop(h, lg, max_iter, &hs, nullptr, s)) != SPG_OK) return st;
-    const bool out_host = !is_device_ptr(p_out);
-    float *od = p_out;
-    if (out_host) { CK(h->stage_out.ensure((size_t)N)); od = h->stage_out.p; }
-    launch_scatter_state(N, h->fwd.d_inv, h->d_state, od, nullptr, 0, s);
-    if (out_host) CK(cudaMemcpyAsync(p_out, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    float *od;
+    bool staged;
+    if ((st = out_target(h, p_out, N, false, &od, &staged, s)) != SPG_OK) return st;
+    launch_unpermute_state(N, h->fwd.d_perm, h->d_state, od, nullptr, 0, s);
+    if (staged) CK(cudaMemcpyAsync(p_out, od, N * sizeof(float), cudaMemcpyDeviceToHost, s));
     std::vector<int32_t> it((size_t)G);
     std::vector<double> l1((size_t)G), dg((size_t)G);
     CK(cudaMemcpyAsync(it.data(), h->d_giters, G * sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -86,9 +86,17 @@ void launch_scatter_axpby(int64_t n, const int32_t *inv, const float *yp, float 
                           float beta, cudaStream_t s);
 void launch_scatter_rows(int64_t n, int k, const int32_t *inv, const float *Yp, float *Y,
                          int64_t ldy, float alpha, float beta, cudaStream_t s);
-// out[inv[k]] = buf[parity][k] * (scale of k's half when hits) from state
-void launch_scatter_state(int64_t n, const int32_t *inv, const IterState *st, float *out,
-                          const uint8_t *row_half, int hits, cudaStream_t s);
+// Caller order <-> position order by perm (perm[j] = position of node j),
+// the caller's side read or written in order (it may be mapped host memory):
+// xp[perm[j]] = x[j] (* d[perm[j]] when d != nullptr);
+void launch_permute_in(int64_t n, const int32_t *perm, const float *x, const float *d, float *xp,
+                       cudaStream_t s);
+// out[j] = buf[parity][perm[j]] (* the scale of its half when hits), from state;
+void launch_unpermute_state(int64_t n, const int32_t *perm, const IterState *st, float *out,
+                            const uint8_t *row_half, int hits, cudaStream_t s);
+// y[j] = alpha yp[perm[j]] + beta y[j] (beta = 0: y not read).
+void launch_unpermute_axpby(int64_t n, const int32_t *perm, const float *yp, float *y, float alpha,
+                            float beta, cudaStream_t s);
 void launch_fill(int64_t n, float v, float *p, cudaStream_t s);
 void launch_onehot_rows(int64_t n, int k, const int32_t *seeds, float *X, cudaStream_t s);
 
