@@ -19,8 +19,8 @@
  *    host pointers (pageable or pinned); the library detects which with
  *    cudaPointerGetAttributes.  Pinned (page-locked, mapped) host vectors
  *    are read (x of spg_spmv, p0 of spg_pagerank, g of spg_rwr_adjoint) and
- *    written (y of spg_spmv, the results of spg_pagerank, spg_rwr with
- *    k = 1, spg_pagerank_ranks and spg_batch_pagerank) by the permutation
+ *    written (y of spg_spmv, the results of spg_pagerank, spg_rwr,
+ *    spg_pagerank_ranks and spg_batch_pagerank) by the permutation
  *    kernels directly over the host link, in order, without a staging copy:
  *    the reordering between node order and the format's position order and
  *    the transfer are one pass.  Pageable host vectors, and the other host

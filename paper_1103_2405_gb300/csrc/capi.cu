@@ -1324,15 +1324,12 @@ extern "C" spg_status spg_rwr(spg_handle h, float restart, const int32_t *seeds,
     if (st != SPG_OK) return st;
     CK(cudaGetLastError());
     if ((st = run_loop(h, g, max_iter, &hs, info, s)) != SPG_OK) return st;
-    const bool out_host = !is_device_ptr(R);
     float *cur = hs.buf[hs.parity];
-    if (out_host) {
-        CK(h->stage_out.ensure((size_t)(N * k)));
-        launch_scatter_rows(N, k, L.d_inv, cur, h->stage_out.p, k, 1.f, 0.f, s);
-        CK(cudaMemcpyAsync(R, h->stage_out.p, N * k * sizeof(float), cudaMemcpyDeviceToHost, s));
-    } else {
-        launch_scatter_rows(N, k, L.d_inv, cur, R, k, 1.f, 0.f, s);
-    }
+    float *od;
+    bool staged;
+    if ((st = out_target(h, R, N * k, false, &od, &staged, s)) != SPG_OK) return st;
+    launch_unpermute_rows(N, k, L.d_perm, cur, od, k, 1.f, 0.f, s);
+    if (staged) CK(cudaMemcpyAsync(R, od, N * k * sizeof(float), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return (tol > 0 && !(hs.l1 < tol)) ? SPG_NOT_CONVERGED : SPG_OK;
 }

@@ -2220,6 +2220,29 @@ void launch_unpermute_axpby(int64_t n, const int32_t *perm, const float *yp, flo
     count_launches(1);
 }
 
+// Rows of an n x k block back to original order: Y[j] = alpha Yp[pi(j)]
+// (+ beta Y[j]), Y written row after row (it may be mapped host memory).
+__global__ void k_unpermute_rows(int64_t n, int k, const int32_t *__restrict__ perm,
+                                 const float *__restrict__ Yp, float *__restrict__ Y, int64_t ldy,
+                                 float alpha, float beta)
+{
+    const int64_t total = n * k;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / k, c = t % k;
+        float *dst = Y + j * ldy + c;
+        const float v = alpha * __ldg(Yp + (int64_t)perm[j] * k + c);
+        *dst = beta != 0.f ? fmaf(beta, *dst, v) : v;
+    }
+}
+
+void launch_unpermute_rows(int64_t n, int k, const int32_t *perm, const float *Yp, float *Y,
+                           int64_t ldy, float alpha, float beta, cudaStream_t s)
+{
+    k_unpermute_rows<<<grid_for(n * k), 256, 0, s>>>(n, k, perm, Yp, Y, ldy, alpha, beta);
+    count_launches(1);
+}
+
 __global__ void k_fill(int64_t n, float v, float *__restrict__ p)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;

@@ -94,9 +94,12 @@ void launch_permute_in(int64_t n, const int32_t *perm, const float *x, const flo
 // out[j] = buf[parity][perm[j]] (* the scale of its half when hits), from state;
 void launch_unpermute_state(int64_t n, const int32_t *perm, const IterState *st, float *out,
                             const uint8_t *row_half, int hits, cudaStream_t s);
-// y[j] = alpha yp[perm[j]] + beta y[j] (beta = 0: y not read).
+// y[j] = alpha yp[perm[j]] + beta y[j] (beta = 0: y not read);
 void launch_unpermute_axpby(int64_t n, const int32_t *perm, const float *yp, float *y, float alpha,
                             float beta, cudaStream_t s);
+// rows of an n x k block: Y[j] (leading dimension ldy) = alpha Yp[perm[j]] + beta Y[j].
+void launch_unpermute_rows(int64_t n, int k, const int32_t *perm, const float *Yp, float *Y,
+                           int64_t ldy, float alpha, float beta, cudaStream_t s);
 void launch_fill(int64_t n, float v, float *p, cudaStream_t s);
 void launch_onehot_rows(int64_t n, int k, const int32_t *seeds, float *X, cudaStream_t s);
 

@@ -70,6 +70,11 @@ def test_rwr_hits_batch_outputs_in_pinned_memory(graph):
     ref, _ = f.rwr([s], 0.15, tol=0.0, max_iter=20, like=like)
     got, _ = f.rwr([s], 0.15, tol=0.0, max_iter=20, out=torch.empty(n).pin_memory())
     assert torch.equal(got, ref.cpu())
+    seeds = graphgen.pick_seeds(rp, 3, 4)
+    Rd, _ = f.rwr(seeds, 0.15, tol=0.0, max_iter=20, like=like)
+    Rp, _ = f.rwr(seeds, 0.15, tol=0.0, max_iter=20, out=torch.empty(n, 3).pin_memory())
+    Rn, _ = f.rwr(seeds, 0.15, tol=0.0, max_iter=20, out=np.empty((n, 3), np.float32))
+    assert torch.equal(Rp, Rd.cpu()) and np.array_equal(Rn, Rd.cpu().numpy())
     fh = spg.Format(rp, col, kind="hits")
     a, h, _ = fh.hits(norm=2, iters=15, like=like)
     ap, hp, _ = fh.hits(norm=2, iters=15, auth=torch.empty(n).pin_memory(), hub=torch.empty(n).pin_memory())
