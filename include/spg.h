@@ -320,7 +320,9 @@ spg_status spg_format_zero_rows(spg_handle h, int64_t *rows);
  * handle's kind).  x, y: n FP32, original order.  beta == 0: y is not read.
  * The product runs one tiled-composite launch per part in order (Solution 1:
  * "we restart a kernel for each tile"), FP32 accumulation, no atomics on y;
- * x is gathered into the permuted order before and y scattered after. */
+ * x is taken into the permuted order before (gathered from device memory,
+ * read in order from pinned host memory) and y gathered back into original
+ * order after (y[j] = alpha y'[pi(j)] + beta y[j], written in order). */
 spg_status spg_spmv(spg_handle h, const float *x, float *y, float alpha, float beta,
                     void *stream);
 
