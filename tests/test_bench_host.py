@@ -44,3 +44,23 @@ def test_traffic_is_reported_only_for_the_recorded_source():
         assert bytes_ > 0
         assert bench.ncu_traffic(w) == (bytes_ if sha == bench.kernel_source_sha() else None)
     assert bench.ncu_traffic("no such workload") is None
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the reference arm (the FP64 oracle, timed on the host) on the small
+    # R-MAT workload: one JSON line with the contract's keys
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "rmat14", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "dtype", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
